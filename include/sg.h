@@ -1,0 +1,178 @@
+/*
+ * sg.h -- C ABI of the GB300 (sm_103a) initial-guess / SEM / Jacobi-PCG library.
+ *
+ * Method: Austin, Chalmers & Warburton, "Initial Guesses for Sequences of
+ * Linear Systems in a GPU-Accelerated Incompressible Flow Solver"
+ * (arXiv:2009.10863).  The problem (Sec. 2) is a sequence A x_k = b_k of SPD
+ * systems, one per time step; each is solved by preconditioned CG (Sec. 5.3)
+ * from an initial guess built from earlier solutions by right-hand-side
+ * projection (Sec. 2, Algorithms 1-2) or by polynomial extrapolation (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *  - Vectors are DEVICE pointers to contiguous arrays of n = sg_op_size(op)
+ *    elements of the handle's dtype (SG_F64: double, SG_F32: float), owned by
+ *    the caller.  They must be 16-byte aligned.  Global node g of an
+ *    ex*ey*ez-element mesh of degree p is g = ix + nx*(iy + ny*iz),
+ *    nx = p*ex + 1 (x fastest).
+ *  - Workspaces are DEVICE buffers owned by the caller, sized by the matching
+ *    *_workspace_bytes() query, 256-byte aligned, and must outlive the handle
+ *    (guess) or the call (PCG).  The library allocates only the small
+ *    per-operator coefficient tables (sg_op_create, < 4 KB).
+ *  - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is stream-ordered and asynchronous unless stated.
+ *  - Return value: SG_OK (0) on success, SG_NOT_CONVERGED (1) as a warning,
+ *    a negative SG_ERR_* code on failure.  On failure handle state is left
+ *    unchanged and sg_last_error() returns a message (thread-local).  Errors
+ *    are reported, never trapped on the device.
+ *  - Dirichlet conditions hold on all six faces of the unit box: the operator
+ *    ignores boundary entries of its input and writes 0 there.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_op_s* sg_op_t;
+typedef struct sg_guess_s* sg_guess_t;
+
+enum sg_dtype { SG_F64 = 0, SG_F32 = 1 };
+
+/* Guess methods (Sec. 4, Table 1 nomenclature). */
+enum sg_method {
+  SG_ZERO = 0,          /* x0 = 0                                            */
+  SG_LAST = 1,          /* x0 = x_{k-1} (degree-0 extrapolation, Sec. 3.1)   */
+  SG_EXTRAP = 2,        /* EXTRAP(m, s): least squares, Eq. LSQRCoeffs       */
+  SG_PROJ_QR = 3,       /* QR(s): rolling-QR projection, Algorithm 2         */
+  SG_PROJ_CLASSIC = 4,  /* CLASSIC(s): restarted projection, Algorithm 1     */
+  SG_SPEXTRAP = 5       /* SPEXTRAP(m, s): sparse, Eq. CPQRCoeffs            */
+};
+
+/* PCG stopping rules (Sec. 6.4). */
+enum sg_criterion {
+  SG_STOP_REL_B = 0,      /* ||r|| <= tol * ||b||                            */
+  SG_STOP_INITRESID = 1,  /* ||r|| <  tol * max(||r0||, 1), Eq. StopCritINITRESID */
+  SG_STOP_RHS = 2         /* ||r|| <  tol * max(||b||, 1),  Eq. StopCritRHS  */
+};
+
+enum sg_status {
+  SG_OK = 0,
+  SG_NOT_CONVERGED = 1,   /* PCG hit maxit; x holds the last iterate        */
+  SG_ERR_INVALID = -1,    /* bad argument (size, alignment, dtype, range)    */
+  SG_ERR_CUDA = -2,       /* a CUDA runtime call failed                      */
+  SG_ERR_BREAKDOWN = -3,  /* PCG: p^T A p <= 0 or a non-finite value         */
+  SG_ERR_STATE = -5       /* call not valid for this handle/method           */
+};
+
+#define SG_MAX_HISTORY 16 /* largest history size s                         */
+#define SG_MAX_DEGREE 8   /* largest GLL degree p                           */
+
+int sg_version(void);
+const char* sg_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Operator: matrix-free GLL spectral-element A = K + lambda*M on the unit
+ * box split into ex*ey*ez equal axis-aligned hexahedra, degree p
+ * (Sec. 5.1; Helmholtz form of Eq. VelocityEqn, Poisson form of Eq.
+ * PressureEqn with lambda = 0).  K is the GLL-quadrature stiffness matrix,
+ * M the diagonal GLL mass matrix, both assembled by gather-scatter.
+ * ------------------------------------------------------------------------ */
+
+/* Create an operator.  1 <= p <= SG_MAX_DEGREE, ex,ey,ez >= 1, lambda >= 0,
+ * dtype SG_F64 or SG_F32 (arithmetic and storage type of sg_sem_apply and
+ * sg_pcg_solve).  Allocates < 4 KB of device tables on the current device. */
+int sg_op_create(sg_op_t* op, int ex, int ey, int ez, int p, double lambda, int dtype);
+int sg_op_destroy(sg_op_t op);
+/* n = (p*ex+1)(p*ey+1)(p*ez+1); returns -1 for a NULL handle. */
+int64_t sg_op_size(sg_op_t op);
+/* Host copies of the 1D GLL nodes and weights on [-1,1] (p+1 each). */
+int sg_op_gll(sg_op_t op, double* nodes, double* weights);
+
+/* y = A x (Sec. 5.1).  x, y: device, n elements, must not alias. */
+int sg_sem_apply(sg_op_t op, const void* x, void* y, void* stream);
+
+/* diag(A) with 1 on Dirichlet nodes (the Jacobi preconditioner, Sec. 5.3). */
+int sg_op_diagonal(sg_op_t op, void* diag, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Jacobi-preconditioned CG (Sec. 5.3) with the stopping rules of Sec. 6.4.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace sg_pcg_solve needs for this operator. */
+size_t sg_pcg_workspace_bytes(sg_op_t op);
+
+/* Solve A x = b.  b: device input; x: device, initial guess on entry,
+ * solution on exit (Dirichlet entries set to 0).  tol > 0, maxit >= 0,
+ * criterion from sg_criterion.  workspace: device, sg_pcg_workspace_bytes.
+ * iters, relres: HOST outputs (may be NULL) -- the iteration count and the
+ * final true relative residual ||b - A x|| / ||b||.  The call synchronises
+ * with ``stream`` (the host polls convergence every few iterations).
+ * Returns SG_OK, SG_NOT_CONVERGED (maxit reached) or SG_ERR_BREAKDOWN. */
+int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
+                 void* workspace, int* iters, double* relres, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Initial guesses (Sec. 2-3).  A guess handle keeps the history spaces in
+ * the caller's workspace: for EXTRAP/SPEXTRAP/LAST a ring of s solutions
+ * (Sec. 3, Eq. ExtrapExpn); for PROJ_QR/PROJ_CLASSIC the right-hand-side
+ * basis B~ and solutions X~ (A X~ = B~, B~ orthonormal) plus the triangular
+ * factor R (Sec. 2, Algorithms 1-2).  All control state (d, R, ring head)
+ * stays on the device, so form/update never synchronise.
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes for a guess handle of this size/method/dtype. */
+size_t sg_guess_workspace_bytes(int64_t n, int s, int method, int dtype);
+
+/* Create a guess handle.  1 <= s <= SG_MAX_HISTORY (history size M);
+ * degree_m: extrapolation degree (0 <= m <= s-1; -1 selects floor(sqrt(s)));
+ * eps_rel: projection rejection threshold -- a new direction is kept only if
+ * ||b~|| after CGS2 exceeds eps_rel * ||A x|| (Sec. 2, "small relative to
+ * b"); op: required for PROJ_* (the update forms b~ = A x, Algorithm 2),
+ * ignored otherwise; workspace: device, sg_guess_workspace_bytes bytes, zeroed
+ * by this call (stream-ordered on the legacy default stream). */
+int sg_guess_create(sg_guess_t* g, int64_t n, int s, int method, int degree_m, double eps_rel,
+                    sg_op_t op, void* workspace, int dtype);
+int sg_guess_destroy(sg_guess_t g);
+
+/* Form the initial guess for right-hand side b (Algorithm 2 first line, or
+ * Eq. ExtrapExpn).  With no history yet, x0 is left as passed in (the
+ * caller's arbitrary x0, Sec. 2 notation); ZERO writes 0.  b, x0: device.
+ * x0 may be the pointer returned by sg_guess_next_slot. */
+int sg_guess_form(sg_guess_t g, const void* b, void* x0, void* stream);
+
+/* EXTRAP/SPEXTRAP/LAST: device pointer of the ring slot the next solution
+ * will occupy.  A solver that leaves x_k there makes the history update free
+ * (App. A: "stores the solutions in place").  NULL for other methods. */
+void* sg_guess_next_slot(sg_guess_t g);
+
+/* Add solution x (of A x = b) to the history.  EXTRAP: copies x into the
+ * next slot unless x already is that slot.  PROJ_QR: Algorithm 2 after the
+ * solve -- b~ = A x, Givens downdate when d = M, CGS2, rejection test.
+ * PROJ_CLASSIC: Algorithm 1 after the solve.  b is not read. */
+int sg_guess_update(sg_guess_t g, const void* x, const void* b, void* stream);
+
+/* Debug/inspection (synchronises ``stream``): current history dimension d
+ * (PROJ) or stored-solution count (EXTRAP), and, if R is not NULL, the
+ * s*s row-major FP64 factor R (PROJ) or the current s coefficients beta
+ * (EXTRAP, oldest first, zero-padded). */
+int sg_guess_info(sg_guess_t g, int* d, double* R, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (library-side CUDA events around the launches of one kernel
+ * class, recorded on the launching stream).  kernel ids: 0 sem_apply,
+ * 1 pcg_apply (operator + fused p-update), 2 pcg_update, 3 extrap,
+ * 4 proj_dots, 5 proj_lincomb, 6 proj_update (Givens + CGS2 sweeps).
+ * ------------------------------------------------------------------------ */
+int sg_profile_enable(int on);
+/* Synchronises; total milliseconds and launch count since the last reset. */
+int sg_profile_read(int kernel_id, double* total_ms, long long* launches);
+int sg_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

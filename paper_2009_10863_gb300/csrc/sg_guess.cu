@@ -1,0 +1,715 @@
+// sg_guess.cu -- initial guesses: extrapolation (Sec. 3) and right-hand-side
+// projection (Sec. 2, Algorithms 1 and 2).
+//
+// Extrapolation keeps a ring of the last s solutions; the guess is one
+// streaming pass x0 = sum_i beta_i x_{ring(i)} (Eq. ExtrapExpn) with beta
+// from Eq. LSQRCoeffs (or Eq. CPQRCoeffs, zero terms skipped).
+//
+// Projection keeps B~ (orthonormal right-hand-side basis) and X~ (A X~ = B~)
+// in s physical column slots, logical column j = scale_j * slot_j.  Storing
+// the new column unnormalised with scale 1/||b~|| folds the normalisation
+// (paper kernel rhsUpdateSpace) into the last Gram-Schmidt sweep.  The
+// update (Algorithm 2 after the solve) is four launches:
+//   sem_apply : t = A x_k
+//   upd1      : [d = M: drop column 1 of R, d-1 Givens rotations of the column
+//               pairs of B~ and X~ in one register-carried sweep] + c1 = B~^T t,
+//               ||t||^2                          (rhsQRUpdate + rhsProject)
+//   upd2      : t -= B~ c1, c2 = B~^T t          (rhsReconstruct + rhsProject)
+//   upd3      : t -= B~ c2 -> slot d of B~; x~ = x_k - X~ (c1 + c2) -> slot d
+//               of X~; ||t||^2; accept if ||t|| > eps ||A x_k||, d++
+// The x~ updates of both CGS passes are merged into one (X~ is not modified
+// in between).  All control (d, R, Givens parameters, the eps test) runs in
+// the last CTA of each sweep, so nothing synchronises with the host.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sg_sem_launch.cuh"
+
+namespace sgb {
+int lsq_beta(int M, int m, double* beta);
+int sparse_beta(int M, int m, double* beta);
+}
+
+namespace {
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr int NV = SG_SMAX + 1;   // dots + one norm per reduction
+}
+
+struct ProjState {
+  int d, accepted, rotated, pad;
+  double R[SG_SMAX * SG_SMAX];   // row-major, R[i*SMAX + j]
+  double scale[SG_SMAX];
+  double c1[SG_SMAX], c2[SG_SMAX], alpha[SG_SMAX];
+  double nrm0sq, nrmsq;
+  unsigned int counter[4];
+};
+
+struct sg_guess_s {
+  int method, s, m, dtype, nsl;   // nsl: ring slots (EXTRAP family)
+  int64_t n;
+  double eps_rel;
+  sg_op_t op;
+  unsigned char* ws;
+  size_t off_state, off_partials, off_a, off_b, off_t, slot_bytes;
+  int blocks;
+  int count, next;                // ring bookkeeping (host mirror, deterministic)
+  double beta_tab[SG_SMAX + 1][SG_SMAX];
+};
+
+template <typename T> struct VecT;
+template <> struct VecT<double> { using V = double2; static constexpr int W = 2; };
+template <> struct VecT<float> { using V = float4; static constexpr int W = 4; };
+
+// lane accessors; w is a compile-time constant after unrolling, so the
+// vectors stay in registers
+__device__ __forceinline__ double& vel(double2& v, int w) { return w == 0 ? v.x : v.y; }
+__device__ __forceinline__ float& vel(float4& v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ double vel(const double2& v, int w) { return w == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vel(const float4& v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+template <typename V> __device__ __forceinline__ V vzero() { V v; for (int w = 0; w < (int)(sizeof(V) / sizeof(v.x)); ++w) vel(v, w) = 0; return v; }
+
+// ---------------------------------------------------------------- extrapolation
+template <typename T>
+struct ExtrapArgs {
+  const T* src[SG_SMAX];
+  double beta[SG_SMAX];
+  int k;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_extrap(T* out, const ExtrapArgs<T> a, int n) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  T b[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) b[j] = (T)a.beta[j];
+  const int nv = n / W;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V acc = vzero<V>();
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < a.k) {
+        const V v = reinterpret_cast<const V*>(a.src[j])[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) vel(acc, w) += b[j] * vel(v, w);
+      }
+    }
+    reinterpret_cast<V*>(out)[i] = acc;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j)
+      if (j < a.k) acc += b[j] * a.src[j][i];
+    out[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- projection kernels
+template <typename T>
+struct ProjArgs {
+  T* B;              // slot 0 of B~ (slot j at B + j*stride)
+  T* X;              // slot 0 of X~
+  T* t;              // temporary right-hand side (b~ during the update)
+  const T* v;        // form: b;  upd3: x_k
+  T* out;            // form: x0
+  size_t stride;     // elements between slots
+  int n, M, classic;
+  double eps_rel;
+  ProjState* st;
+  double* partials;
+};
+
+template <typename T>
+__device__ __forceinline__ const typename VecT<T>::V* colv(const T* base, size_t stride, int j) {
+  return reinterpret_cast<const typename VecT<T>::V*>(base + (size_t)j * stride);
+}
+
+// form, pass 1: alpha_j = scale_j * (slot_j . b), j < d
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_dots(const ProjArgs<T> a) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  __shared__ double sred[32 * NV];
+  const int d = a.st->d;
+  T acc[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const V bv = reinterpret_cast<const V*>(a.v)[i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        const V cv = colv(a.B, a.stride, j)[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(bv, w);
+      }
+    }
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j)
+      if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * a.v[i];
+  }
+  double v[NV], tot[NV];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
+  v[SG_SMAX] = 0.0;
+  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+    if (threadIdx.x == 0)
+      for (int j = 0; j < d; ++j) a.st->alpha[j] = a.st->scale[j] * tot[j];
+  }
+}
+
+// form, pass 2: x0 = sum_j alpha_j scale_j slot_j of X~ (x0 untouched if d = 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_lincomb(const ProjArgs<T> a) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  const int d = a.st->d;
+  if (d == 0) return;
+  T c[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->alpha[j] * a.st->scale[j]) : (T)0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V acc = vzero<V>();
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        const V xv = colv(a.X, a.stride, j)[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) vel(acc, w) += c[j] * vel(xv, w);
+      }
+    }
+    reinterpret_cast<V*>(a.out)[i] = acc;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j)
+      if (j < d) acc += c[j] * a.X[(size_t)j * a.stride + i];
+    a.out[i] = acc;
+  }
+}
+
+// One Givens sweep over a column set at vector index i (App. A: the column
+// shared by successive rotations stays in registers).  Writes new columns
+// 0..d-1; returns nothing for X~, accumulates dots with t for B~.
+template <typename T, bool DOTS>
+__device__ __forceinline__ void givens_sweep_vec(T* base, size_t stride, int i, int d,
+                                                 const T* sc0, const T* gc, const T* gs,
+                                                 const T* gcin, const T* gsin,
+                                                 const typename VecT<T>::V& tv, T* acc) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  V carry = reinterpret_cast<const V*>(base)[i];
+#pragma unroll
+  for (int w = 0; w < W; ++w) vel(carry, w) *= sc0[0];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX - 1; ++j) {
+    if (j < d) {
+      const V nx = colv(base, stride, j + 1)[i];
+      V o;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const T cw = vel(carry, w), nw = vel(nx, w);
+        vel(o, w) = gc[j] * cw + gsin[j] * nw;
+        vel(carry, w) = -gs[j] * cw + gcin[j] * nw;
+        if (DOTS) acc[j] += vel(o, w) * vel(tv, w);
+      }
+      reinterpret_cast<V*>(base + (size_t)j * stride)[i] = o;
+    }
+  }
+}
+
+template <typename T, bool DOTS>
+__device__ __forceinline__ void givens_sweep_scalar(T* base, size_t stride, int i, int d,
+                                                    T sc0, const T* gc, const T* gs,
+                                                    const T* gcin, const T* gsin, T tt, T* acc) {
+  T carry = sc0 * base[i];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX - 1; ++j) {
+    if (j < d) {
+      const T nx = base[(size_t)(j + 1) * stride + i];
+      const T o = gc[j] * carry + gsin[j] * nx;
+      carry = -gs[j] * carry + gcin[j] * nx;
+      if (DOTS) acc[j] += o * tt;
+      base[(size_t)j * stride + i] = o;
+    }
+  }
+}
+
+// update sweep 1: optional Givens downdate (Algorithm 2, d = M) or classic
+// restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  __shared__ double sred[32 * NV];
+  __shared__ double sR[SG_SMAX * SG_SMAX];
+  __shared__ T s_cin[SG_SMAX], s_sin[SG_SMAX], s_c[SG_SMAX], s_s[SG_SMAX], s_sc[SG_SMAX];
+  __shared__ int s_d, s_rot;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const ProjState* st = a.st;
+    int d = st->d;
+    int rot = 0;
+    if (a.classic) {
+      if (d >= a.M) d = 0;   // hard restart: the new vector starts a fresh space
+    } else if (d == a.M && d > 1) {
+      rot = 1;
+      // R <- R(:, 2:d): a d x (d-1) upper Hessenberg matrix
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d - 1; ++j) sR[i * SG_SMAX + j] = st->R[i * SG_SMAX + j + 1];
+      for (int i = 0; i < d - 1; ++i) {
+        double av = sR[i * SG_SMAX + i], bv = sR[(i + 1) * SG_SMAX + i];
+        double r = hypot(av, bv);
+        double c = 1.0, s = 0.0;
+        if (r > 0.0) { c = fabs(av) / r; s = (av >= 0.0 ? 1.0 : -1.0) * bv / r; }
+        for (int j = i; j < d - 1; ++j) {
+          double u = sR[i * SG_SMAX + j], w = sR[(i + 1) * SG_SMAX + j];
+          sR[i * SG_SMAX + j] = c * u + s * w;
+          sR[(i + 1) * SG_SMAX + j] = -s * u + c * w;
+        }
+        // new_i = c L_i + s L_{i+1}, carry = -s L_i + c L_{i+1}; the incoming
+        // physical slot i+1 carries its column scale
+        s_c[i] = (T)c;
+        s_s[i] = (T)s;
+        s_cin[i] = (T)(c * st->scale[i + 1]);
+        s_sin[i] = (T)(s * st->scale[i + 1]);
+      }
+      s_sc[0] = (T)st->scale[0];
+    } else if (d == a.M && d == 1) {
+      d = 0;   // dropping the only column leaves an empty space
+    }
+    s_d = rot ? d - 1 : d;   // columns the new vector is projected on
+    s_rot = rot;
+  }
+  __syncthreads();
+  const int d = s_d;
+  const int rot = s_rot;
+  T acc[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
+  T nn = 0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const V tv = reinterpret_cast<const V*>(a.t)[i];
+#pragma unroll
+    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+    if (rot) {
+      givens_sweep_vec<T, true>(a.B, a.stride, i, d, s_sc, s_c, s_s, s_cin, s_sin, tv, acc);
+      givens_sweep_vec<T, false>(a.X, a.stride, i, d, s_sc, s_c, s_s, s_cin, s_sin, tv, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < SG_SMAX; ++j) {
+        if (j < d) {
+          const V cv = colv(a.B, a.stride, j)[i];
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(tv, w);
+        }
+      }
+    }
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const T tt = a.t[i];
+    nn += tt * tt;
+    if (rot) {
+      givens_sweep_scalar<T, true>(a.B, a.stride, i, d, s_sc[0], s_c, s_s, s_cin, s_sin, tt, acc);
+      givens_sweep_scalar<T, false>(a.X, a.stride, i, d, s_sc[0], s_c, s_s, s_cin, s_sin, tt, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < SG_SMAX; ++j)
+        if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
+    }
+  }
+  double v[NV], tot[NV];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
+  v[SG_SMAX] = (double)nn;
+  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+    if (tid == 0) {
+      ProjState* st = a.st;
+      if (rot) {
+        for (int i = 0; i < SG_SMAX * SG_SMAX; ++i) st->R[i] = 0.0;
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) st->R[i * SG_SMAX + j] = sR[i * SG_SMAX + j];
+        for (int j = 0; j < SG_SMAX; ++j) st->scale[j] = 1.0;
+        for (int j = 0; j < d; ++j) st->c1[j] = tot[j];
+      } else {
+        for (int j = 0; j < d; ++j) st->c1[j] = st->scale[j] * tot[j];
+      }
+      st->d = d;
+      st->rotated = rot;
+      st->nrm0sq = tot[SG_SMAX];
+    }
+  }
+}
+
+// update sweep 2: t -= B~ c1; c2 = B~^T t
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  __shared__ double sred[32 * NV];
+  const int d = a.st->d;
+  T c[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->c1[j] * a.st->scale[j]) : (T)0;
+  T acc[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V tv = reinterpret_cast<const V*>(a.t)[i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        const V b = colv(a.B, a.stride, j)[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) vel(tv, w) -= c[j] * vel(b, w);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        const V b = colv(a.B, a.stride, j)[i];   // L1 hit
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j] += vel(b, w) * vel(tv, w);
+      }
+    }
+    reinterpret_cast<V*>(a.t)[i] = tv;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    T tt = a.t[i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j)
+      if (j < d) tt -= c[j] * a.B[(size_t)j * a.stride + i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j)
+      if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
+    a.t[i] = tt;
+  }
+  double v[NV], tot[NV];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
+  v[SG_SMAX] = 0.0;
+  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+    if (threadIdx.x == 0)
+      for (int j = 0; j < d; ++j) a.st->c2[j] = a.st->scale[j] * tot[j];
+  }
+}
+
+// update sweep 3: b~ = t - B~ c2 -> B~ slot d; x~ = x_k - X~ (c1 + c2) -> X~ slot d;
+// ||b~||^2; acceptance test and R column (Algorithm 2, last block)
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  __shared__ double sred[32 * NV];
+  const int d = a.st->d;
+  T c2[SG_SMAX], cx[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) {
+    c2[j] = (j < d) ? (T)(a.st->c2[j] * a.st->scale[j]) : (T)0;
+    cx[j] = (j < d) ? (T)((a.st->c1[j] + a.st->c2[j]) * a.st->scale[j]) : (T)0;
+  }
+  T* Bd = a.B + (size_t)d * a.stride;
+  T* Xd = a.X + (size_t)d * a.stride;
+  T nn = 0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V tv = reinterpret_cast<const V*>(a.t)[i];
+    V xv = reinterpret_cast<const V*>(a.v)[i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        const V bc = colv(a.B, a.stride, j)[i];
+        const V xc = colv(a.X, a.stride, j)[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          vel(tv, w) -= c2[j] * vel(bc, w);
+          vel(xv, w) -= cx[j] * vel(xc, w);
+        }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+    reinterpret_cast<V*>(Bd)[i] = tv;
+    reinterpret_cast<V*>(Xd)[i] = xv;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    T tt = a.t[i], xx = a.v[i];
+#pragma unroll
+    for (int j = 0; j < SG_SMAX; ++j) {
+      if (j < d) {
+        tt -= c2[j] * a.B[(size_t)j * a.stride + i];
+        xx -= cx[j] * a.X[(size_t)j * a.stride + i];
+      }
+    }
+    nn += tt * tt;
+    Bd[i] = tt;
+    Xd[i] = xx;
+  }
+  double v[NV], tot[NV];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
+  v[SG_SMAX] = (double)nn;
+  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+    if (threadIdx.x == 0) {
+      ProjState* st = a.st;
+      const double nb = sqrt(tot[SG_SMAX]);
+      st->nrmsq = tot[SG_SMAX];
+      const bool accept = (d == 0) ? (nb > 0.0) : (nb > a.eps_rel * sqrt(st->nrm0sq));
+      st->accepted = accept ? 1 : 0;
+      if (accept && isfinite(nb)) {
+        for (int j = 0; j < d; ++j) st->R[j * SG_SMAX + d] = st->c1[j] + st->c2[j];
+        st->R[d * SG_SMAX + d] = nb;
+        st->scale[d] = 1.0 / nb;
+        st->d = d + 1;
+      }
+    }
+  }
+}
+
+__global__ void k_proj_init(ProjState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->d = 0; st->accepted = 0; st->rotated = 0;
+    for (int i = 0; i < SG_SMAX * SG_SMAX; ++i) st->R[i] = 0.0;
+    for (int j = 0; j < SG_SMAX; ++j) { st->scale[j] = 1.0; st->c1[j] = st->c2[j] = st->alpha[j] = 0.0; }
+    st->nrm0sq = st->nrmsq = 0.0;
+    for (int i = 0; i < 4; ++i) st->counter[i] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+bool is_ring(int m) { return m == SG_EXTRAP || m == SG_SPEXTRAP || m == SG_LAST; }
+bool is_proj(int m) { return m == SG_PROJ_QR || m == SG_PROJ_CLASSIC; }
+
+int reduce_blocks(int64_t n, int W) {
+  int64_t b = ((n + W - 1) / W + 255) / 256;
+  int64_t cap = 4LL * sg_num_sms();
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+struct GuessLayout { size_t state, partials, a, b, t, slot, total; int blocks, nsl; };
+
+GuessLayout guess_layout(int64_t n, int s, int method, int dtype) {
+  GuessLayout L{};
+  const size_t es = dtype == SG_F64 ? 8 : 4;
+  const int W = dtype == SG_F64 ? 2 : 4;
+  L.slot = align_up(es * (size_t)n);
+  L.blocks = reduce_blocks(n, W);
+  L.nsl = (method == SG_LAST) ? 1 : s;
+  size_t off = 0;
+  L.state = off; off += align_up(sizeof(ProjState));
+  L.partials = off; off += align_up(sizeof(double) * NV * (size_t)L.blocks);
+  L.a = off;
+  if (is_ring(method)) { off += L.slot * L.nsl; L.b = off; L.t = off; }
+  else if (is_proj(method)) { off += L.slot * s; L.b = off; off += L.slot * s; L.t = off; off += L.slot; }
+  else { L.b = off; L.t = off; }
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+ProjArgs<T> proj_args(sg_guess_t g) {
+  ProjArgs<T> a{};
+  a.B = reinterpret_cast<T*>(g->ws + g->off_a);
+  a.X = reinterpret_cast<T*>(g->ws + g->off_b);
+  a.t = reinterpret_cast<T*>(g->ws + g->off_t);
+  a.stride = g->slot_bytes / sizeof(T);
+  a.n = (int)g->n;
+  a.M = g->s;
+  a.classic = g->method == SG_PROJ_CLASSIC;
+  a.eps_rel = g->eps_rel;
+  a.st = reinterpret_cast<ProjState*>(g->ws + g->off_state);
+  a.partials = reinterpret_cast<double*>(g->ws + g->off_partials);
+  return a;
+}
+
+template <typename T>
+int extrap_form(sg_guess_t g, void* x0, cudaStream_t s) {
+  if (g->count == 0) return SG_OK;
+  ExtrapArgs<T> a{};
+  const int k = g->count;
+  const double* beta = g->beta_tab[k];
+  int nt = 0;
+  for (int i = 0; i < k; ++i) {   // i = 0 oldest
+    if (beta[i] == 0.0) continue;   // sparse extrapolation: skip zero terms
+    int slot = ((g->next - k + i) % g->nsl + g->nsl) % g->nsl;
+    a.src[nt] = reinterpret_cast<const T*>(g->ws + g->off_a + (size_t)slot * g->slot_bytes);
+    a.beta[nt] = beta[i];
+    ++nt;
+  }
+  a.k = nt;
+  ProfScope ps(PROF_EXTRAP, s);
+  k_extrap<T><<<reduce_blocks(g->n, VecT<T>::W) * 2, 256, 0, s>>>(static_cast<T*>(x0), a, (int)g->n);
+  SG_LAUNCH_CHECK("k_extrap");
+  return SG_OK;
+}
+
+template <typename T>
+int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
+  ProjArgs<T> a = proj_args<T>(g);
+  a.v = static_cast<const T*>(b);
+  a.out = static_cast<T*>(x0);
+  const int nb = reduce_blocks(g->n, VecT<T>::W);
+  {
+    ProfScope ps(PROF_PROJ_DOTS, s);
+    k_proj_dots<T><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_dots");
+  }
+  {
+    ProfScope ps(PROF_PROJ_LINCOMB, s);
+    k_proj_lincomb<T><<<nb * 2, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_lincomb");
+  }
+  return SG_OK;
+}
+
+template <typename T>
+int proj_update(sg_guess_t g, const void* x, cudaStream_t s) {
+  ProjArgs<T> a = proj_args<T>(g);
+  a.v = static_cast<const T*>(x);
+  int rc = sg_sem_apply(g->op, x, a.t, s);
+  if (rc) return rc;
+  const int nb = reduce_blocks(g->n, VecT<T>::W);
+  ProfScope ps(PROF_PROJ_UPDATE, s);
+  k_proj_upd1<T><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd1");
+  k_proj_upd2<T><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd2");
+  k_proj_upd3<T><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd3");
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" size_t sg_guess_workspace_bytes(int64_t n, int s, int method, int dtype) {
+  if (n < 1 || s < 1 || s > SG_SMAX || method < 0 || method > 5 || (dtype != SG_F64 && dtype != SG_F32)) return 0;
+  return guess_layout(n, s, method, dtype).total;
+}
+
+extern "C" int sg_guess_create(sg_guess_t* out, int64_t n, int s, int method, int degree_m,
+                               double eps_rel, sg_op_t op, void* workspace, int dtype) {
+  if (!out) return sg_fail(SG_ERR_INVALID, "guess_create: NULL output handle");
+  *out = nullptr;
+  if (n < 1 || n >= (1LL << 31)) return sg_fail(SG_ERR_INVALID, "guess_create: n out of range");
+  if (s < 1 || s > SG_SMAX) return sg_fail(SG_ERR_INVALID, "guess_create: s must be in [1, 16]");
+  if (method < 0 || method > 5) return sg_fail(SG_ERR_INVALID, "guess_create: unknown method");
+  if (dtype != SG_F64 && dtype != SG_F32) return sg_fail(SG_ERR_INVALID, "guess_create: bad dtype");
+  if (is_proj(method)) {
+    if (!op) return sg_fail(SG_ERR_INVALID, "guess_create: projection needs the operator");
+    if (op->n != n || op->dtype != dtype) return sg_fail(SG_ERR_INVALID, "guess_create: operator size/dtype mismatch");
+    if (!(eps_rel >= 0.0)) return sg_fail(SG_ERR_INVALID, "guess_create: eps_rel must be >= 0");
+  }
+  int m = degree_m;
+  if (m < 0) { m = 0; while ((m + 1) * (m + 1) <= s) ++m; }   // floor(sqrt(s))
+  if ((method == SG_EXTRAP || method == SG_SPEXTRAP) && m > s - 1)
+    return sg_fail(SG_ERR_INVALID, "guess_create: degree m must be <= s-1");
+  GuessLayout L = guess_layout(n, s, method, dtype);
+  if (L.total > 0 && !workspace) return sg_fail(SG_ERR_INVALID, "guess_create: NULL workspace");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return sg_fail(SG_ERR_INVALID, "guess_create: workspace must be 256-byte aligned");
+  sg_guess_s* g = new sg_guess_s();
+  g->method = method; g->s = s; g->m = m; g->dtype = dtype; g->n = n;
+  g->eps_rel = eps_rel; g->op = op;
+  g->ws = static_cast<unsigned char*>(workspace);
+  g->off_state = L.state; g->off_partials = L.partials; g->off_a = L.a; g->off_b = L.b; g->off_t = L.t;
+  g->slot_bytes = L.slot; g->blocks = L.blocks; g->nsl = L.nsl;
+  g->count = 0; g->next = 0;
+  std::memset(g->beta_tab, 0, sizeof(g->beta_tab));
+  if (method == SG_LAST) {
+    g->beta_tab[1][0] = 1.0;
+  } else if (method == SG_EXTRAP || method == SG_SPEXTRAP) {
+    for (int k = 1; k <= s; ++k) {
+      int mk = m < k - 1 ? m : k - 1;
+      int rc = (method == SG_EXTRAP) ? sgb::lsq_beta(k, mk, g->beta_tab[k])
+                                     : sgb::sparse_beta(k, mk, g->beta_tab[k]);
+      if (rc) { delete g; return sg_fail(SG_ERR_INVALID, "guess_create: coefficient computation failed"); }
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(g->ws, 0, L.total, 0);
+  if (e == cudaSuccess && is_proj(method)) {
+    k_proj_init<<<1, 32>>>(reinterpret_cast<ProjState*>(g->ws + g->off_state));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) { delete g; return sg_fail(SG_ERR_CUDA, std::string("guess_create: ") + cudaGetErrorString(e)); }
+  *out = g;
+  return SG_OK;
+}
+
+extern "C" int sg_guess_destroy(sg_guess_t g) { delete g; return SG_OK; }
+
+extern "C" void* sg_guess_next_slot(sg_guess_t g) {
+  if (!g || !is_ring(g->method)) return nullptr;
+  return g->ws + g->off_a + (size_t)g->next * g->slot_bytes;
+}
+
+extern "C" int sg_guess_form(sg_guess_t g, const void* b, void* x0, void* stream) {
+  if (!g || !x0) return sg_fail(SG_ERR_INVALID, "guess_form: NULL argument");
+  if (!aligned16(x0) || (b && !aligned16(b))) return sg_fail(SG_ERR_INVALID, "guess_form: vectors must be 16-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  const size_t es = g->dtype == SG_F64 ? 8 : 4;
+  if (g->method == SG_ZERO) {
+    SG_CUDA_TRY(cudaMemsetAsync(x0, 0, es * (size_t)g->n, s));
+    return SG_OK;
+  }
+  if (is_ring(g->method))
+    return g->dtype == SG_F64 ? extrap_form<double>(g, x0, s) : extrap_form<float>(g, x0, s);
+  if (!b) return sg_fail(SG_ERR_INVALID, "guess_form: projection needs b");
+  return g->dtype == SG_F64 ? proj_form<double>(g, b, x0, s) : proj_form<float>(g, b, x0, s);
+}
+
+extern "C" int sg_guess_update(sg_guess_t g, const void* x, const void* b, void* stream) {
+  (void)b;
+  if (!g || !x) return sg_fail(SG_ERR_INVALID, "guess_update: NULL argument");
+  if (!aligned16(x)) return sg_fail(SG_ERR_INVALID, "guess_update: x must be 16-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  if (g->method == SG_ZERO) return SG_OK;
+  if (is_ring(g->method)) {
+    void* slot = sg_guess_next_slot(g);
+    if (slot != x)
+      SG_CUDA_TRY(cudaMemcpyAsync(slot, x, (g->dtype == SG_F64 ? 8 : 4) * (size_t)g->n,
+                                  cudaMemcpyDeviceToDevice, s));
+    g->next = (g->next + 1) % g->nsl;
+    if (g->count < g->nsl) g->count += 1;
+    return SG_OK;
+  }
+  return g->dtype == SG_F64 ? proj_update<double>(g, x, s) : proj_update<float>(g, x, s);
+}
+
+extern "C" int sg_guess_info(sg_guess_t g, int* d, double* R, void* stream) {
+  if (!g) return sg_fail(SG_ERR_INVALID, "guess_info: NULL handle");
+  cudaStream_t s = as_stream(stream);
+  if (is_proj(g->method)) {
+    ProjState h;
+    SG_CUDA_TRY(cudaMemcpyAsync(&h, g->ws + g->off_state, sizeof(ProjState), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (d) *d = h.d;
+    if (R)
+      for (int i = 0; i < g->s; ++i)
+        for (int j = 0; j < g->s; ++j) R[i * g->s + j] = h.R[i * SG_SMAX + j];
+    return SG_OK;
+  }
+  if (d) *d = g->count;
+  if (R) {
+    for (int i = 0; i < g->s; ++i) R[i] = 0.0;
+    for (int i = 0; i < g->count && i < g->s; ++i) R[i] = g->beta_tab[g->count][i];
+  }
+  return SG_OK;
+}

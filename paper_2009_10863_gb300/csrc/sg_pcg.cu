@@ -1,0 +1,280 @@
+// sg_pcg.cu -- fused Jacobi-PCG (Sec. 5.3) with the stopping rules of Sec. 6.4.
+//
+// Per iteration two launches, all scalars kept on the device:
+//   k_sem<MODE 1>:  p = z + beta p (p = z first), q = A p, p.q -> alpha = (r.z)/(p.q)
+//   k_pcg_update:   x += alpha p, r -= alpha q, z = r / diag(A), r.r, r.z
+//                   -> convergence test on ||r||, beta = (r.z)_new / (r.z)
+// The host launches a chunk of iterations and then reads the done flag once;
+// kernels after convergence return immediately.  Vector traffic: 12 n words
+// per iteration (4 in the operator kernel, 8 in the update).
+#include <map>
+#include <mutex>
+
+#include "sg_sem_launch.cuh"
+
+int sg_op_diag_launch(sg_op_t op, void* out, int inverse, cudaStream_t s);
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct PcgLayout {
+  size_t state, partials, r, z, pa, pb, q, invd, total;
+  int max_blocks;
+};
+
+int update_blocks(int64_t n, int vec) {
+  int64_t nv = (n + vec - 1) / vec;
+  int64_t b = (nv + 255) / 256;
+  int64_t cap = 8LL * sg_num_sms();
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+int sem_ctas(const SemGeom& g) {
+  int tex = 1, tey = 1;
+  switch (g.p) {
+#define SG_CASE(P) case P: tex = SemTile<P>::TEX; tey = SemTile<P>::TEY; break;
+    SG_CASE(1) SG_CASE(2) SG_CASE(3) SG_CASE(4) SG_CASE(5) SG_CASE(6) SG_CASE(7) SG_CASE(8)
+#undef SG_CASE
+  }
+  int zl = sg_sem_layers(g, tex, tey, 0);
+  return ((g.ex + tex - 1) / tex) * ((g.ey + tey - 1) / tey) * ((g.ez + zl - 1) / zl);
+}
+
+PcgLayout layout_for(sg_op_t op) {
+  PcgLayout L{};
+  const size_t es = op->dtype == SG_F64 ? 8 : 4;
+  const size_t vb = align_up(es * (size_t)op->n);
+  int mb = sem_ctas(op->g);
+  int ub = update_blocks(op->n, op->dtype == SG_F64 ? 2 : 4);
+  L.max_blocks = mb > ub ? mb : ub;
+  size_t off = 0;
+  L.state = off; off += align_up(sizeof(PcgState));
+  L.partials = off; off += align_up(sizeof(double) * 4 * (size_t)L.max_blocks);
+  L.r = off; off += vb;
+  L.z = off; off += vb;
+  L.pa = off; off += vb;
+  L.pb = off; off += vb;
+  L.q = off; off += vb;
+  L.invd = off; off += vb;
+  L.total = off;
+  return L;
+}
+
+// which operator last wrote 1/diag into a workspace (host-side bookkeeping)
+std::mutex g_ws_mu;
+std::map<void*, const void*> g_ws_owner;
+
+struct PollBuf { int iter, done, status, pad; };
+
+}  // namespace
+
+template <typename T>
+__global__ void k_mask_faces(T* v, int nx, int ny, int nz) {
+  const size_t nxy = (size_t)nx * ny;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = t0; i < nx * ny; i += stride) {          // z faces
+    v[i] = (T)0;
+    v[(size_t)(nz - 1) * nxy + i] = (T)0;
+  }
+  for (int i = t0; i < nx * nz; i += stride) {          // y faces
+    int xi = i % nx, zi = i / nx;
+    v[(size_t)zi * nxy + xi] = (T)0;
+    v[(size_t)zi * nxy + (size_t)(ny - 1) * nx + xi] = (T)0;
+  }
+  for (int i = t0; i < ny * nz; i += stride) {          // x faces
+    int yi = i % ny, zi = i / ny;
+    v[(size_t)zi * nxy + (size_t)yi * nx] = (T)0;
+    v[(size_t)zi * nxy + (size_t)yi * nx + nx - 1] = (T)0;
+  }
+}
+
+__global__ void k_pcg_setup(PcgState* st, double tol, int maxit, int criterion) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->rz = st->pq = st->rr = st->bb = st->rr0 = st->thr2 = 0.0;
+    st->alpha = st->beta = st->rr_true = 0.0;
+    st->iter = 0; st->done = 0; st->status = PCG_RUNNING; st->first = 1;
+    st->maxit = maxit; st->criterion = criterion; st->tol = tol;
+    for (int i = 0; i < 4; ++i) st->counter[i] = 0u;
+  }
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<double> { using V = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
+
+template <typename T>
+__device__ __forceinline__ void upd1(T& x, T p, T& r, T q, T id, T& z, T al, T& rr, T& rz) {
+  x += al * p;
+  r -= al * q;
+  z = r * id;
+  rr += r * r;
+  rz += r * z;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pcg_update(T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r, const T* __restrict__ q,
+             const T* __restrict__ invd, T* __restrict__ z, int n, PcgState* st, double* partials) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+  __shared__ int s_skip;
+  __shared__ double s_alpha;
+  __shared__ double sred[64];
+  if (threadIdx.x == 0) { s_skip = st->done; s_alpha = st->alpha; }
+  __syncthreads();
+  if (s_skip) return;
+  const T al = (T)s_alpha;
+  T rr = 0, rz = 0;
+  const int nv = n / W;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V xv = reinterpret_cast<V*>(x)[i];
+    V pv = reinterpret_cast<const V*>(p)[i];
+    V rv = reinterpret_cast<V*>(r)[i];
+    V qv = reinterpret_cast<const V*>(q)[i];
+    V dv = reinterpret_cast<const V*>(invd)[i];
+    V zv;
+    upd1(xv.x, pv.x, rv.x, qv.x, dv.x, zv.x, al, rr, rz);
+    upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, rr, rz);
+    if constexpr (W == 4) {
+      upd1(xv.z, pv.z, rv.z, qv.z, dv.z, zv.z, al, rr, rz);
+      upd1(xv.w, pv.w, rv.w, qv.w, dv.w, zv.w, al, rr, rz);
+    }
+    reinterpret_cast<V*>(x)[i] = xv;
+    reinterpret_cast<V*>(r)[i] = rv;
+    reinterpret_cast<V*>(z)[i] = zv;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    T xs = x[i], rs = r[i], zs;
+    upd1(xs, p[i], rs, q[i], invd[i], zs, al, rr, rz);
+    x[i] = xs; r[i] = rs; z[i] = zs;
+  }
+  double v[2] = {(double)rr, (double)rz}, tot[2];
+  if (grid_reduce_last<2>(v, partials, &st->counter[1], sred, tot)) {
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      st->rr = tot[0];
+      const bool strict = st->criterion != SG_STOP_REL_B;
+      const bool conv = strict ? (tot[0] < st->thr2) : (tot[0] <= st->thr2);
+      if (!isfinite(tot[0]) || !isfinite(tot[1])) { st->status = PCG_BREAKDOWN; st->done = 1; }
+      else if (conv) { st->status = PCG_CONVERGED; st->done = 1; }
+      else {
+        st->beta = tot[1] / st->rz;
+        st->rz = tot[1];
+        if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
+      }
+    }
+  }
+}
+
+template <typename T>
+static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion,
+                   unsigned char* ws, const PcgLayout& L, int* iters, double* relres, cudaStream_t s) {
+  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
+  double* partials = reinterpret_cast<double*>(ws + L.partials);
+  T* r = reinterpret_cast<T*>(ws + L.r);
+  T* z = reinterpret_cast<T*>(ws + L.z);
+  T* pb[2] = {reinterpret_cast<T*>(ws + L.pa), reinterpret_cast<T*>(ws + L.pb)};
+  T* q = reinterpret_cast<T*>(ws + L.q);
+  T* invd = reinterpret_cast<T*>(ws + L.invd);
+  const int n = (int)op->n;
+  const SemGeom& g = op->g;
+
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto it = g_ws_owner.find(ws);
+    if (it == g_ws_owner.end() || it->second != (const void*)op) {
+      int rc = sg_op_diag_launch(op, invd, 1, s);
+      if (rc) return rc;
+      g_ws_owner[ws] = op;
+    }
+  }
+  k_mask_faces<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz);
+  SG_LAUNCH_CHECK("k_mask_faces");
+  k_pcg_setup<<<1, 32, 0, s>>>(st, tol, maxit, criterion);
+  SG_LAUNCH_CHECK("k_pcg_setup");
+  {
+    SemArgs<T> a{};
+    a.x = x; a.aux = b; a.invd = invd; a.out = r; a.out2 = z;
+    a.partials = partials; a.st = st; a.final_pass = 0;
+    int rc = sg_sem_launch<T, 2>(g, a, s, 0);
+    if (rc) return rc;
+  }
+  const int ub = update_blocks(op->n, Vec<T>::W);
+  static thread_local PollBuf* poll = nullptr;
+  if (!poll) SG_CUDA_TRY(cudaHostAlloc((void**)&poll, sizeof(PollBuf), cudaHostAllocDefault));
+  int launched = 0, chunk = 4;
+  while (true) {
+    SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (poll->done) break;
+    if (launched >= maxit) break;   // defensive; the device sets done at maxit
+    const int k = (chunk < maxit - launched) ? chunk : (maxit - launched);
+    for (int i = 0; i < k; ++i) {
+      const int it = launched + i;
+      T* pnew = pb[it & 1];
+      const T* pold = pb[(it + 1) & 1];
+      {
+        ProfScope ps(PROF_PCG_APPLY, s);
+        SemArgs<T> a{};
+        a.x = z; a.aux = pold; a.out = q; a.out2 = pnew;
+        a.partials = partials; a.st = st;
+        int rc = sg_sem_launch<T, 1>(g, a, s, 0);
+        if (rc) return rc;
+      }
+      {
+        ProfScope ps(PROF_PCG_UPDATE, s);
+        k_pcg_update<T><<<ub, 256, 0, s>>>(x, pnew, r, q, invd, z, n, st, partials);
+        SG_LAUNCH_CHECK("k_pcg_update");
+      }
+    }
+    launched += k;
+    if (chunk < 16) chunk *= 2;
+  }
+  // true residual ||b - A x|| / ||b||
+  {
+    SemArgs<T> a{};
+    a.x = x; a.aux = b; a.invd = invd; a.out = r; a.out2 = z;
+    a.partials = partials; a.st = st; a.final_pass = 1;
+    int rc = sg_sem_launch<T, 2>(g, a, s, 0);
+    if (rc) return rc;
+  }
+  PcgState hs;
+  SG_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (iters) *iters = hs.iter;
+  if (relres) *relres = hs.bb > 0 ? sqrt(hs.rr_true / hs.bb) : sqrt(hs.rr_true);
+  if (hs.status == PCG_BREAKDOWN) return sg_fail(SG_ERR_BREAKDOWN, "pcg: breakdown (p^T A p <= 0 or non-finite value)");
+  if (hs.status == PCG_MAXIT || hs.status == PCG_RUNNING) {
+    sg_set_error("pcg: maximum iteration count reached");
+    return SG_NOT_CONVERGED;
+  }
+  return SG_OK;
+}
+
+extern "C" size_t sg_pcg_workspace_bytes(sg_op_t op) {
+  if (!op) return 0;
+  return layout_for(op).total;
+}
+
+extern "C" int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
+                            void* workspace, int* iters, double* relres, void* stream) {
+  if (!op || !b || !x || !workspace) return sg_fail(SG_ERR_INVALID, "pcg_solve: NULL argument");
+  if (!(tol > 0.0)) return sg_fail(SG_ERR_INVALID, "pcg_solve: tol must be > 0");
+  if (maxit < 0) return sg_fail(SG_ERR_INVALID, "pcg_solve: maxit must be >= 0");
+  if (criterion < 0 || criterion > 2) return sg_fail(SG_ERR_INVALID, "pcg_solve: unknown criterion");
+  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, "pcg_solve: vectors must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "pcg_solve: workspace must be 256-byte aligned");
+  if (b == x) return sg_fail(SG_ERR_INVALID, "pcg_solve: b and x must not alias");
+  PcgLayout L = layout_for(op);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  cudaStream_t s = as_stream(stream);
+  if (op->dtype == SG_F64)
+    return pcg_run<double>(op, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit,
+                           criterion, ws, L, iters, relres, s);
+  return pcg_run<float>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit,
+                        criterion, ws, L, iters, relres, s);
+}

@@ -1,0 +1,51 @@
+// sg_sem_launch.cuh -- host-side dispatch of k_sem over (dtype, degree, mode).
+#pragma once
+#include "sg_sem_kernel.cuh"
+
+// Element layers per CTA: enough CTAs for ~4 per SM, fewer layers means more
+// restaging of the first plane and of the z-carry per chunk.
+int sg_sem_layers(const SemGeom& g, int tex, int tey, int override_zl);
+
+template <typename T, int P, int MODE>
+int sg_sem_launch_p(const SemGeom& g, const SemArgs<T>& a0, cudaStream_t s, int zl_override) {
+  using TL = SemTile<P>;
+  SemArgs<T> a = a0;
+  a.zl = sg_sem_layers(g, TL::TEX, TL::TEY, zl_override);
+  dim3 block(TL::TX, TL::TY, 1);
+  dim3 grid((g.ex + TL::TEX - 1) / TL::TEX, (g.ey + TL::TEY - 1) / TL::TEY,
+            (g.ez + a.zl - 1) / a.zl);
+  const size_t smem = sizeof(T) * (size_t)TL::NPL * TL::PY * TL::PX;
+  static bool attr_set = false;   // one attribute call per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_sem<T, P, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("sem smem attribute: ") + cudaGetErrorString(e));
+    attr_set = true;
+  }
+  k_sem<T, P, MODE><<<grid, block, smem, s>>>(g, a);
+  SG_LAUNCH_CHECK("k_sem");
+  return SG_OK;
+}
+
+template <typename T, int MODE>
+int sg_sem_launch(const SemGeom& g, const SemArgs<T>& a, cudaStream_t s, int zl_override = 0) {
+  switch (g.p) {
+    case 1: return sg_sem_launch_p<T, 1, MODE>(g, a, s, zl_override);
+    case 2: return sg_sem_launch_p<T, 2, MODE>(g, a, s, zl_override);
+    case 3: return sg_sem_launch_p<T, 3, MODE>(g, a, s, zl_override);
+    case 4: return sg_sem_launch_p<T, 4, MODE>(g, a, s, zl_override);
+    case 5: return sg_sem_launch_p<T, 5, MODE>(g, a, s, zl_override);
+    case 6: return sg_sem_launch_p<T, 6, MODE>(g, a, s, zl_override);
+    case 7: return sg_sem_launch_p<T, 7, MODE>(g, a, s, zl_override);
+    case 8: return sg_sem_launch_p<T, 8, MODE>(g, a, s, zl_override);
+    default: return sg_fail(SG_ERR_INVALID, "degree p out of range");
+  }
+}
+
+// explicit instantiations live in sg_sem_f64.cu / sg_sem_f32.cu
+extern template int sg_sem_launch<double, 0>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
+extern template int sg_sem_launch<double, 1>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
+extern template int sg_sem_launch<double, 2>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
+extern template int sg_sem_launch<float, 0>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);
+extern template int sg_sem_launch<float, 1>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);
+extern template int sg_sem_launch<float, 2>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/sg.h declares.
+
+CPU only: no kernel is launched.  The host-side parts of the library (GLL
+nodes/weights, workspace size queries, argument validation) are checked
+against the oracle and the header.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sg.h")
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_2009_10863_gb300 import build as b
+    b.build()
+    import paper_2009_10863_gb300 as sgmod
+    sgmod.lib()
+    return sgmod
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(sg):
+    names = _declared()
+    assert len(names) >= 18
+    L = ctypes.CDLL(sg.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), "missing export " + n
+    bound = {s[0] for s in sg.SIGNATURES}
+    assert set(names) == bound
+
+
+def test_version_and_error_strings(sg):
+    L = sg.lib()
+    assert L.sg_version() == 1
+    h = ctypes.c_void_p()
+    assert L.sg_op_create(ctypes.byref(h), 0, 1, 1, 3, 0.0, 0) == sg.ERR_INVALID
+    assert b"element" in L.sg_last_error()
+    assert L.sg_op_create(ctypes.byref(h), 2, 2, 2, 9, 0.0, 0) == sg.ERR_INVALID
+    assert L.sg_op_create(ctypes.byref(h), 2, 2, 2, 3, -1.0, 0) == sg.ERR_INVALID
+    assert L.sg_op_create(ctypes.byref(h), 2, 2, 2, 3, 0.0, 7) == sg.ERR_INVALID
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_library_gll_matches_oracle(sg, p):
+    """The library's Newton/barycentric GLL nodes and weights agree with the
+    oracle's numpy root-finding implementation."""
+    from oracle.gll import gll_nodes_weights
+    L = sg.lib()
+    h = ctypes.c_void_p()
+    assert L.sg_op_create(ctypes.byref(h), 2, 3, 1, p, 1.0, 0) == 0
+    assert L.sg_op_size(h) == (2 * p + 1) * (3 * p + 1) * (p + 1)
+    x = (ctypes.c_double * (p + 1))()
+    w = (ctypes.c_double * (p + 1))()
+    assert L.sg_op_gll(h, x, w) == 0
+    xo, wo = gll_nodes_weights(p)
+    assert np.allclose(np.array(x[:]), xo, atol=1e-15)
+    assert np.allclose(np.array(w[:]), wo, atol=1e-15)
+    assert L.sg_op_destroy(h) == 0
+
+
+def test_workspace_queries(sg):
+    L = sg.lib()
+    n = 12345
+    ring = L.sg_guess_workspace_bytes(n, 8, sg.EXTRAP, sg.F64)
+    proj = L.sg_guess_workspace_bytes(n, 8, sg.PROJ_QR, sg.F64)
+    ring32 = L.sg_guess_workspace_bytes(n, 8, sg.EXTRAP, sg.F32)
+    assert ring >= 8 * 8 * n and proj >= 17 * 8 * n and proj > 2 * ring * 0.9
+    assert ring32 < ring
+    assert L.sg_guess_workspace_bytes(n, 17, sg.EXTRAP, sg.F64) == 0
+    assert L.sg_guess_workspace_bytes(n, 8, 9, sg.F64) == 0
+    assert L.sg_guess_workspace_bytes(0, 8, sg.EXTRAP, sg.F64) == 0

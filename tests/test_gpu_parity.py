@@ -1,0 +1,364 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Every comparison feeds both sides the same seeded inputs.  Tolerances:
+FP64 operator 1e-13 (relative 2-norm; rounding order only), guesses 1e-12,
+solutions 1e-10, PCG iterations +-1; FP32 paths 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle.sem import SemOperator
+from oracle.pcg import pcg as opcg, REL_B, INITRESID, RHS
+from oracle import extrap as oex
+from oracle.proj import ProjectionQR, ProjectionClassic
+from oracle.sequence import run_sequence
+from synthetic import Modes, random_vectors, CONFIGS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_10863_gb300 import build as b
+    b.build()
+    import paper_2009_10863_gb300 as sgmod
+    sgmod.lib()
+    return sgmod
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+MESHES = [((1, 1, 1), 1, 0.0), ((2, 2, 2), 1, 1.0), ((4, 4, 4), 3, 0.0), ((3, 5, 2), 2, 3.5),
+          ((5, 3, 4), 4, 0.0), ((2, 3, 2), 5, 1e3), ((4, 3, 3), 6, 0.0), ((5, 4, 3), 7, 1e5),
+          ((9, 3, 2), 7, 0.0), ((2, 2, 3), 8, 2.0), ((1, 2, 1), 7, 1.0)]
+
+
+# ---------------------------------------------------------------- operator
+@pytest.mark.parametrize("E,p,lam", MESHES)
+def test_sem_apply_f64(sg, E, p, lam):
+    ref = SemOperator(*E, p, lam)
+    op = sg.Op(*E, p, lam, "f64")
+    x = random_vectors(p * 100 + sum(E), 1, ref.n)[0]      # boundary entries nonzero on purpose
+    want = ref.apply(x)
+    got = host(op.apply(dev(x)))
+    assert rel(got, want) <= 1e-13
+    assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
+    assert np.all(got[~ref.interior] == 0.0)
+
+
+@pytest.mark.parametrize("E,p,lam", MESHES[2::2])
+def test_sem_apply_f32(sg, E, p, lam):
+    ref = SemOperator(*E, p, lam)
+    op = sg.Op(*E, p, lam, "f32")
+    x = np.float32(random_vectors(p + 7, 1, ref.n)[0]).astype(np.float64)
+    want = ref.apply(x)
+    got = host(op.apply(dev(x, torch.float32)))
+    assert rel(got, want) <= 1e-5
+    assert np.all(got[~ref.interior] == 0.0)
+
+
+@pytest.mark.parametrize("E,p,lam", MESHES[::3])
+def test_diagonal(sg, E, p, lam):
+    ref = SemOperator(*E, p, lam)
+    op = sg.Op(*E, p, lam, "f64")
+    assert rel(host(op.diagonal()), ref.diagonal()) <= 1e-14
+
+
+def test_sem_apply_full_size_fp64_helmholtz(sg):
+    """16^3 elements, p = 7, lambda = 1e5: the FP64 Helmholtz operator at full size."""
+    c = CONFIGS["c2"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+    cx, cy, cz = ref.coords_1d()
+    x = Modes(c["seed"], c["modes"], c["kmax"]).field(cx, cy, cz, 0.3)
+    x = x + 1e-3 * random_vectors(9, 1, ref.n)[0]
+    want = ref.apply(x)
+    got = host(op.apply(dev(x)))
+    assert rel(got, want) <= 1e-13
+
+
+def test_sem_apply_full_size_fp32_poisson(sg):
+    """32^3 elements, p = 7 Poisson in FP32 (the mixed-precision operator)."""
+    c = CONFIGS["c3"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    op = sg.Op(*c["E"], c["p"], c["lam"], "f32")
+    # a random field: a smooth one cancels strongly in A x (||A x|| << sum |terms|),
+    # which measures FP32 rounding, not the kernel's indexing
+    x = np.float32(random_vectors(31, 1, ref.n)[0]).astype(np.float64)
+    want = ref.apply(x)
+    got = host(op.apply(dev(x, torch.float32)))
+    assert rel(got, want) <= 1e-5
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
+
+
+# ---------------------------------------------------------------- PCG
+def _problem(E=(4, 4, 4), p=3, lam=0.0, seed=3):
+    ref = SemOperator(*E, p, lam)
+    rng = np.random.default_rng(seed)
+    xs = rng.standard_normal(ref.n) * ref.interior
+    return ref, rng, xs
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+@pytest.mark.parametrize("E,p,lam", [((4, 4, 4), 3, 0.0), ((3, 4, 5), 5, 50.0), ((5, 3, 2), 7, 1e4)])
+def test_pcg_matches_oracle(sg, tol, E, p, lam):
+    ref, rng, xs = _problem(E, p, lam)
+    b = ref.apply(xs) + 0.01 * rng.standard_normal(ref.n) * ref.interior
+    x0 = 0.1 * rng.standard_normal(ref.n) * ref.interior
+    xo, ito, relo, _ = opcg(ref.apply, ref.diagonal(), b, x0, tol, interior=ref.interior)
+    op = sg.Op(*E, p, lam, "f64")
+    x = dev(x0)
+    it, relg = op.pcg(dev(b), x, tol)
+    assert abs(it - ito) <= 1
+    assert relg <= tol * 1.0000001
+    assert rel(host(x), xo) <= max(1e-10, 10 * tol)
+    if it == ito:
+        assert rel(host(x), xo) <= 1e-10
+
+
+@pytest.mark.parametrize("crit", [REL_B, INITRESID, RHS])
+def test_pcg_criteria(sg, crit):
+    ref, rng, xs = _problem((3, 3, 3), 4, 2.0, seed=5)
+    b = ref.apply(xs)
+    x0 = xs + 1e-4 * rng.standard_normal(ref.n) * ref.interior
+    _, ito, _, _ = opcg(ref.apply, ref.diagonal(), b, x0, 1e-8, criterion=crit, interior=ref.interior)
+    op = sg.Op(3, 3, 3, 4, 2.0, "f64")
+    x = dev(x0)
+    it, _ = op.pcg(dev(b), x, 1e-8, criterion=crit)
+    assert abs(it - ito) <= 1
+
+
+def test_pcg_edge_cases(sg):
+    ref, rng, xs = _problem((2, 3, 2), 3, 1.0, seed=6)
+    op = sg.Op(2, 3, 2, 3, 1.0, "f64")
+    b = ref.apply(xs)
+    # exact initial guess: 0 iterations
+    x = dev(xs)
+    it, r = op.pcg(dev(b), x, 1e-10)
+    assert it == 0 and r < 1e-12
+    # b = 0: 0 iterations, x = 0 is returned for x0 = 0
+    x = op.zeros()
+    it, r = op.pcg(op.zeros(), x, 1e-10)
+    assert it == 0 and float(x.abs().max()) == 0.0
+    # maxit cap -> NOT_CONVERGED with exactly maxit iterations
+    x = op.zeros()
+    it, r = op.pcg(dev(b), x, 1e-14, maxit=3)
+    assert it == 3 and r > 1e-14
+    with pytest.raises(sg.SGError):
+        op.pcg(dev(b), op.zeros(), 1e-14, maxit=3, raise_on_maxit=True)
+    # boundary entries of the initial guess are zeroed
+    x0 = xs + 5.0 * (~ref.interior)
+    x = dev(x0)
+    op.pcg(dev(b), x, 1e-10)
+    assert np.all(host(x)[~ref.interior] == 0.0)
+
+
+def test_pcg_single_element_all_boundary(sg):
+    """One element of degree 1: every node is a Dirichlet node (n = 8)."""
+    op = sg.Op(1, 1, 1, 1, 0.0, "f64")
+    x = op.zeros()
+    it, r = op.pcg(op.zeros(), x, 1e-10)
+    assert it == 0
+    y = op.apply(dev(np.arange(8.0)))
+    assert float(y.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- extrapolation
+@pytest.mark.parametrize("method,s,m", [("extrap", 4, 2), ("extrap", 8, 2), ("extrap", 8, 3),
+                                        ("extrap", 6, 5), ("spextrap", 8, 2), ("spextrap", 12, 3),
+                                        ("last", 4, 0), ("extrap", 1, 0)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_extrap_sequence(sg, method, s, m, dtype):
+    n = 3001                                   # ragged: not a multiple of the vector width
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    g = sg.Guess(n, s, method, m=m, dtype=dtype)
+    hist = random_vectors(11, s + 5, n)
+    if dtype == "f32":
+        hist = np.float32(hist).astype(np.float64)
+    ringh = []
+    tolr = 1e-12 if dtype == "f64" else 1e-5
+    for k in range(s + 5):
+        x0 = torch.full((n,), 7.0, dtype=tdt, device="cuda")
+        g.form(None, x0)
+        if k == 0:
+            assert float((x0 - 7.0).abs().max()) == 0.0      # no history: x0 untouched
+        else:
+            if method == "last":
+                want = ringh[-1]
+            else:
+                beta = oex.startup_coeffs(len(ringh), s, m, sparse=(method == "spextrap"))
+                want = oex.extrap_guess(ringh, beta)
+            assert rel(host(x0), want) <= tolr
+        # in-place protocol on even steps, copy on odd steps
+        if k % 2 == 0:
+            slot = g.next_slot()
+            slot.copy_(dev(hist[k], tdt))
+            g.update(slot)
+        else:
+            g.update(dev(hist[k], tdt))
+        ringh.append(hist[k])
+        keep = 1 if method == "last" else s
+        ringh = ringh[-keep:]
+
+
+def test_extrap_inplace_guess_into_next_slot(sg):
+    """Guess formed straight into the slot that holds the oldest solution."""
+    n, s, m = 1000, 4, 2
+    g = sg.Guess(n, s, "extrap", m=m)
+    hist = random_vectors(12, 6, n)
+    for k in range(4):
+        g.update(dev(hist[k]))
+    slot = g.next_slot()
+    g.form(None, slot)
+    want = oex.extrap_guess(list(hist[:4]), oex.lsq_coeffs(4, 2))
+    assert rel(host(slot), want) <= 1e-12
+
+
+def test_zero_guess(sg):
+    g = sg.Guess(100, 4, "zero")
+    x0 = torch.ones(100, dtype=torch.float64, device="cuda")
+    g.form(None, x0)
+    assert float(x0.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- projection
+def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dtype="f64"):
+    ref = SemOperator(*E, p, lam)
+    op = sg.Op(*E, p, lam, dtype)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    # the rejection threshold must sit above the storage precision's noise:
+    # an in-span vector leaves ||b~|| / ||A x|| ~ 1e-7 after CGS2 in FP32
+    eps = 1e-10 if dtype == "f64" else 1e-4
+    g = sg.Guess(ref.n, M, method, eps_rel=eps, op=op, dtype=dtype)
+    o = klass(M, eps, ref.apply)
+    rng = np.random.default_rng(21)
+    base = rng.standard_normal((3, ref.n)) * ref.interior
+    tolr = 1e-12 if dtype == "f64" else 2e-4
+    prev = []
+    for k in range(steps):
+        b = ref.apply(rng.standard_normal(ref.n) * ref.interior)
+        x0 = torch.full((ref.n,), 3.0, dtype=tdt, device="cuda")
+        g.form(dev(b, tdt), x0)
+        want = o.form(b, np.full(ref.n, 3.0))
+        assert rel(host(x0), want) <= tolr, "guess at step %d" % k
+        if k == 6:   # a combination of earlier solutions (rejected when in the window)
+            x = 0.5 * prev[-1] + 0.25 * prev[-2]
+        else:
+            x = (np.cos(0.3 * k) * base[0] + np.sin(0.2 * k) * base[1] + 0.1 * k * base[2]
+                 + 1e-3 * rng.standard_normal(ref.n) * ref.interior)
+        if dtype == "f32":
+            x = np.float32(x).astype(np.float64)
+        g.update(dev(x, tdt))
+        o.update(x)
+        prev.append(x)
+        d, R = g.info()
+        assert d == o.d, "d at step %d" % k
+        if method == "qr" and dtype == "f64":
+            Ro = o.R[:d, :d]
+            assert np.allclose(R[:d, :d], Ro, rtol=1e-10, atol=1e-10 * np.abs(Ro).max())
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_proj_qr_sequence(sg, M):
+    _proj_sequence(sg, ProjectionQR, "qr", M)
+
+
+def test_proj_qr_sequence_f32(sg):
+    _proj_sequence(sg, ProjectionQR, "qr", 4, dtype="f32")
+
+
+@pytest.mark.parametrize("M", [1, 3, 4])
+def test_proj_classic_sequence(sg, M):
+    _proj_sequence(sg, ProjectionClassic, "classic", M)
+
+
+def test_proj_rejects_dependent_vector(sg):
+    ref = SemOperator(3, 2, 2, 3, 1.0)
+    op = sg.Op(3, 2, 2, 3, 1.0, "f64")
+    g = sg.Guess(ref.n, 4, "qr", eps_rel=1e-8, op=op)
+    rng = np.random.default_rng(2)
+    xs = rng.standard_normal((2, ref.n)) * ref.interior
+    for x in xs:
+        g.update(dev(x))
+    assert g.info()[0] == 2
+    g.update(dev(0.3 * xs[0] - 2.0 * xs[1]))
+    assert g.info()[0] == 2
+    # b in the span -> the guess is the exact solution
+    xin = 1.5 * xs[0] + 0.25 * xs[1]
+    x0 = op.zeros()
+    g.form(dev(ref.apply(xin)), x0)
+    assert rel(host(x0), xin) <= 1e-12
+
+
+def test_proj_full_size(sg):
+    """QR(8) at 16^3 elements, p = 7 (1.44M nodes): ten updates, guesses vs the oracle."""
+    c = CONFIGS["c2"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+    cx, cy, cz = ref.coords_1d()
+    modes = Modes(c["seed"], 12, c["kmax"])
+    g = sg.Guess(ref.n, 8, "qr", eps_rel=1e-10, op=op)
+    o = ProjectionQR(8, 1e-10, ref.apply)
+    rng = np.random.default_rng(5)
+    for k in range(10):
+        x = modes.field(cx, cy, cz, 0.01 * k) * ref.interior + 1e-6 * rng.standard_normal(ref.n) * ref.interior
+        g.update(dev(x))
+        o.update(x)
+    b = ref.apply(modes.field(cx, cy, cz, 0.1) * ref.interior)
+    x0 = op.zeros()
+    g.form(dev(b), x0)
+    assert g.info()[0] == o.d == 8
+    assert rel(host(x0), o.form(b, np.zeros(ref.n))) <= 1e-12
+
+
+# ---------------------------------------------------------------- whole sequence
+def _gpu_sequence(sg, c, method, s, m, rhs, dtype="f64"):
+    op = sg.Op(*c["E"], c["p"], c["lam"], dtype)
+    g = sg.Guess(op.n, s, method, m=m, eps_rel=c["tol"], op=op)
+    out = []
+    for b in rhs:
+        bd = dev(b)
+        x = g.next_slot() if method in ("extrap", "last", "spextrap") else op.zeros()
+        if x is None:
+            x = op.zeros()
+        if method == "zero":
+            x.zero_()
+        g.form(bd, x)
+        it, r = op.pcg(bd, x, c["tol"])
+        g.update(x)
+        out.append((it, r, host(x)))
+    return out
+
+
+@pytest.mark.parametrize("method,mcode", [("zero", 0), ("last", 1), ("extrap", 2), ("qr", 3)])
+def test_c1_sequence_end_to_end(sg, method, mcode):
+    """The 4^3-element, p = 3 Poisson sequence (20 steps, s = 4, tol 1e-8)."""
+    c = CONFIGS["c1"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    cx, cy, cz = ref.coords_1d()
+    modes = Modes(c["seed"], c["modes"], c["kmax"])
+    rhs = [ref.apply(modes.field(cx, cy, cz, c["dt"] * k) * ref.interior) for k in range(1, c["steps"] + 1)]
+    o = run_sequence(ref, rhs, mcode, c["s"], m=2, tol=c["tol"], keep=True)
+    gres = _gpu_sequence(sg, c, method, c["s"], 2, rhs)
+    for k, (rec, (it, r, x)) in enumerate(zip(o, gres)):
+        assert abs(it - rec["iters"]) <= 1, "step %d: %d vs %d" % (k, it, rec["iters"])
+        assert r <= c["tol"] * 1.000001
+        assert rel(x, rec["x"]) <= 1e-6
+    # the better guesses must cut iterations versus the zero guess
+    if method in ("extrap", "qr"):
+        assert sum(t[0] for t in gres[8:]) < sum(rec["iters"] for rec in run_sequence(ref, rhs, 0, 4, tol=c["tol"])[8:])
