@@ -1,0 +1,400 @@
+"""Benchmark: ms per time-step solve at 1e-10 relative residual, CG iterations,
+and guess-kernel HBM bandwidth, on one GB300 (or N replicas).
+
+Workload (one "step" = form guess + Jacobi-PCG solve + history update, i.e.
+one pass of the whole hot path over one right-hand side):
+  FP64 Helmholtz -Lap + lambda on 16x16x16 elements, p = 7 (113^3 = 1,442,897
+  nodes), lambda = 1/(nu dt) = 1e5; b_k = A x*(t_k) + noise, x* = 32 seeded
+  space-time sine modes, noise std 1e-6 RMS(A x*); history s = 8; PCG to
+  ||r|| <= 1e-10 ||b||.  Headline guess: EXTRAP(2, 8) (stabilised least
+  squares, Sec. 3.2); ZERO, LAST and QR(8) (Algorithm 2) are reported beside.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import CONFIGS, Modes, noise  # noqa: E402
+
+METRIC = "ms per time-step solve at 1e-10 rel. residual + CG iters; guess-kernel HBM GB/s"
+CFG = CONFIGS["c2"]
+HEADLINE = ("extrap", 2)          # EXTRAP(m=2, s=8)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_name():
+    E = CFG["E"]
+    return "helmholtz-%dx%dx%d-p%d-fp64-%s" % (E[0], E[1], E[2], CFG["p"], "extrap(2,8)")
+
+
+def sem_flops_per_node(p):
+    """Algorithmic flops per node of one assembled sum-factorised operator
+    application on the affine box: per direction an element-line dot of p+1
+    terms (plus the neighbouring element's line for the 1/p shared nodes and
+    the z-carry), i.e. 3 (p+1)(1 + 1/p) FMAs, plus mass term and two weight
+    multiplies."""
+    return 2.0 * 3.0 * (p + 1) * (1.0 + 1.0 / p) + 4.0
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+class Workload:
+    """Right-hand sides b_k = A x*(t_k) + noise built on the device (untimed)."""
+
+    def __init__(self, sg, torch, nsteps, device):
+        self.torch = torch
+        c = CFG
+        self.op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+        cx, cy, cz = self.op.coords_1d()
+        modes = Modes(c["seed"], c["modes"], c["kmax"])
+        sx, sy, sz = modes.factors(cx, cy, cz)
+        n = self.op.n
+        phi = torch.empty((c["modes"], n), dtype=torch.float64, device=device)
+        aphi = torch.empty_like(phi)
+        for j in range(c["modes"]):
+            f = np.einsum('k,y,x->kyx', sz[j], sy[j], sx[j]).reshape(-1)
+            phi[j].copy_(torch.from_numpy(f))
+            self.op.apply(phi[j], out=aphi[j])
+        self.rhs = []
+        for k in range(1, nsteps + 1):
+            amp = torch.from_numpy(modes.amplitudes(c["dt"] * k)).to(device)
+            b = amp @ aphi
+            if c["noise"] > 0:
+                rms = torch.sqrt(torch.mean(b * b))
+                eta = torch.from_numpy(noise(c["seed"], k, n)).to(device)
+                mask = (b != 0).to(torch.float64)
+                b = b + c["noise"] * rms * eta * mask
+            self.rhs.append(b.contiguous())
+        torch.cuda.synchronize()
+
+
+def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, clocks=None, e2e=False):
+    """Run warmup + steps time steps; returns per-step ms, iterations, residuals."""
+    op = wl.op
+    tol = CFG["tol"]
+    g = sg.Guess(op.n, s, method, m=m, eps_rel=tol, op=op, dtype="f64")
+    xbuf = op.zeros()
+    ring = method in ("extrap", "last", "spextrap")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters, rels = [], []
+    host_b = host_x = dev_b = None
+    if e2e:
+        host_b = [wl.rhs[k].cpu().pin_memory() for k in range(warmup + steps)]
+        host_x = torch.empty(op.n, dtype=torch.float64).pin_memory()
+        dev_b = op.empty()
+    launches = 0
+    for k in range(warmup + steps):
+        timed = k >= warmup
+        if timed and k == warmup:
+            torch.cuda.synchronize()
+            if prof:
+                sg.profile_reset()
+                sg.profile_enable(True)
+            if clocks:
+                clocks.start()
+            launches = sg.launch_count()
+        if timed:
+            ev[k - warmup][0].record()
+        if e2e:
+            dev_b.copy_(host_b[k], non_blocking=True)
+            b = dev_b
+        else:
+            b = wl.rhs[k]
+        x = g.next_slot() if ring else xbuf
+        if method == "zero":
+            x.zero_()
+        g.form(b, x)
+        it, r = op.pcg(b, x, tol)
+        g.update(x)
+        if e2e:
+            host_x.copy_(x, non_blocking=True)
+        if timed:
+            ev[k - warmup][1].record()
+            iters.append(it)
+            rels.append(r)
+        flush()
+    torch.cuda.synchronize()
+    launches = sg.launch_count() - launches
+    if prof:
+        sg.profile_enable(False)
+    clk = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"ms": ms, "iters": iters, "rels": rels, "launches": launches, "clocks": clk}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(iters_per_step, samples=3, full_iteration_count=False):
+    """Time the FP64 CPU oracle on the same workload: EXTRAP(2,8) guess, PCG
+    start-up and PCG iterations, composed into ms per step."""
+    from oracle.sem import SemOperator
+    from oracle.pcg import pcg
+    from oracle import extrap as ex
+    c = CFG
+    op = SemOperator(*c["E"], c["p"], c["lam"])
+    cx, cy, cz = op.coords_1d()
+    modes = Modes(c["seed"], c["modes"], c["kmax"])
+    s, m = c["s"], HEADLINE[1]
+    hist = [modes.field(cx, cy, cz, c["dt"] * k) * op.interior for k in range(1, s + 1)]
+    diag = op.diagonal()
+    beta = ex.lsq_coeffs(s, m)
+
+    def rhs(k):
+        b = op.apply(modes.field(cx, cy, cz, c["dt"] * k) * op.interior)
+        rms = np.sqrt(np.mean(b * b))
+        return b + c["noise"] * rms * noise(c["seed"], k, op.n) * (b != 0)
+
+    iters_oracle = None
+    if full_iteration_count:
+        b = rhs(s + 1)
+        x0 = ex.extrap_guess(hist, beta)
+        _, iters_oracle, _, _ = pcg(op.apply, diag, b, x0, c["tol"], interior=op.interior)
+        iters_per_step = iters_oracle
+    t_form, t_init, t_it = [], [], []
+    S = 2
+    for k in range(samples):
+        b = rhs(s + 2 + k)
+        t0 = time.perf_counter()
+        x0 = ex.extrap_guess(hist, beta)
+        t1 = time.perf_counter()
+        pcg(op.apply, diag, b, x0, c["tol"], maxit=0, interior=op.interior)
+        t2 = time.perf_counter()
+        pcg(op.apply, diag, b, x0, c["tol"], maxit=S, interior=op.interior)
+        t3 = time.perf_counter()
+        t_form.append(t1 - t0)
+        t_init.append(t2 - t1)
+        t_it.append(((t3 - t2) - (t2 - t1)) / S)
+    mean = lambda v: sum(v) / len(v)
+    ms = 1e3 * (mean(t_form) + mean(t_init) + iters_per_step * mean(t_it))
+    return ms, iters_per_step, iters_oracle, len(t_form)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    ms, its, its_o, ns = oracle_sample(None, samples=max(1, min(args.steps, 5)), full_iteration_count=True)
+    sample = ("FP64 numpy oracle (single thread) on the 16^3 p=7 Helmholtz workload: one full PCG solve "
+              "from the EXTRAP(2,8) guess gives %d iterations; %d sampled steps time the guess, the PCG "
+              "start-up and 2 PCG iterations, composed into ms per step" % (its_o, ns))
+    line = {"metric": METRIC, "value": ms, "unit": "ms/step", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_name(), "elements": list(CFG["E"]), "p": CFG["p"],
+                       "nodes": (7 * 16 + 1) ** 3, "lambda": CFG["lam"], "s": CFG["s"], "tol": CFG["tol"],
+                       "parallelism": "replicas"},
+            "cg_iters_per_step": its,
+            "cpu_baseline": {"value": ms, "unit": "ms/step", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the ZERO/LAST/QR comparison runs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2009_10863_gb300 as sg
+    from paper_2009_10863_gb300 import build as sgbuild
+    if rank == 0 or world == 1:
+        sgbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        sgbuild.build()
+    sg.lib()
+    device = torch.device("cuda", local)
+    nsteps = args.warmup + args.steps
+    wl = Workload(sg, torch, nsteps, device)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        flush_buf.zero_()
+
+    s = CFG["s"]
+    n = wl.op.n
+    # headline: EXTRAP(2, 8), timed K steps bracketed by barrier + synchronize
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    t_wall = time.perf_counter()
+    head = run_method(sg, torch, wl, HEADLINE[0], HEADLINE[1], s, args.steps, args.warmup, flush,
+                      prof=True, clocks=clocks)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    ms_step = sum(head["ms"]) / len(head["ms"])
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # kernel timing from the library's events (same timed region)
+    prof = {}
+    for name, kid in (("sem", sg.PROF_SEM), ("pcg_apply", sg.PROF_PCG_APPLY), ("pcg_update", sg.PROF_PCG_UPDATE),
+                      ("extrap", sg.PROF_EXTRAP)):
+        tot, cnt = sg.profile_read(kid)
+        prof[name] = (tot, cnt)
+    p = CFG["p"]
+    tot_apply, cnt_apply = prof["pcg_apply"]
+    avg_apply_ms = tot_apply / max(cnt_apply, 1)
+    flop_apply = sem_flops_per_node(p) * n
+    achieved = flop_apply / (avg_apply_ms * 1e-3) / 1e12
+    hbm_gbs, hbm_src = peaks()
+    ex_tot, ex_cnt = prof["extrap"]
+    ex_bytes = (s + 1) * 8 * n
+    ex_gbs = ex_bytes / (ex_tot / max(ex_cnt, 1) * 1e-3) / 1e9 if ex_cnt else None
+    up_tot, up_cnt = prof["pcg_update"]
+    up_gbs = 8 * 8 * n / (up_tot / max(up_cnt, 1) * 1e-3) / 1e9 if up_cnt else None
+
+    out = {"metric": METRIC, "value": ms_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(), "elements": list(CFG["E"]), "p": p, "nodes": n,
+                      "lambda": CFG["lam"], "s": s, "method": "EXTRAP(2,8)", "tol": CFG["tol"],
+                      "criterion": "||r|| <= tol ||b||", "l2": "flushed (512 MiB write) between timed steps",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "cg_iters_per_step": sum(head["iters"]) / len(head["iters"]),
+           "max_relres": max(head["rels"]),
+           "timed_wall_s": t_wall}
+
+    out["roofline"] = {"kernel": "pcg_apply (SEM operator + fused p update, FP64)", "bound": "alu",
+                       "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                       "flops_per_launch": flop_apply, "avg_launch_ms": avg_apply_ms, "launches": cnt_apply,
+                       "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+    out["guess_kernels"] = {
+        "extrap": {"GB_s": ex_gbs, "frac_of_hbm": ex_gbs / hbm_gbs if ex_gbs else None,
+                   "bytes_per_launch": ex_bytes, "launches": ex_cnt},
+        "pcg_update": {"GB_s": up_gbs, "frac_of_hbm": up_gbs / hbm_gbs if up_gbs else None,
+                       "bytes_per_launch": 8 * 8 * n, "launches": up_cnt},
+        "hbm_peak_GB_s": hbm_gbs, "hbm_peak_source": hbm_src}
+    out["gpu_launches"] = head["launches"]
+    if head["clocks"]:
+        out["clocks"] = head["clocks"]
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = run_method(sg, torch, wl, HEADLINE[0], HEADLINE[1], s, args.steps, args.warmup, flush, e2e=True)
+    e2e_ms = sum(e2e["ms"]) / len(e2e["ms"])
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    out["e2e"] = {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    # the other guess methods on the same sequence (not part of the headline)
+    if not args.no_compare:
+        comp = {}
+        for name, m in (("zero", 0), ("last", 0), ("qr", 0)):
+            r = run_method(sg, torch, wl, name, m, s, args.steps, args.warmup, flush)
+            comp[name] = {"ms_per_step": sum(r["ms"]) / len(r["ms"]),
+                          "cg_iters_per_step": sum(r["iters"]) / len(r["iters"])}
+        comp["extrap(2,8)"] = {"ms_per_step": ms_step, "cg_iters_per_step": out["cg_iters_per_step"]}
+        out["methods"] = comp
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_cpu, its, _, ns = oracle_sample(out["cg_iters_per_step"], samples=3)
+        out["cpu_baseline"] = {"value": ms_cpu, "unit": "ms/step", "cores": 1, "kind": "oracle",
+                               "sample": "FP64 numpy oracle (single thread), 16^3 p=7 Helmholtz: %d samples "
+                                         "of the EXTRAP(2,8) guess, PCG start-up and 2 PCG iterations, "
+                                         "composed with %.1f iterations per step" % (ns, its)}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

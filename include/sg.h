@@ -171,6 +171,8 @@ int sg_profile_enable(int on);
 /* Synchronises; total milliseconds and launch count since the last reset. */
 int sg_profile_read(int kernel_id, double* total_ms, long long* launches);
 int sg_profile_reset(void);
+/* Number of kernels this library has launched in the process so far. */
+long long sg_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("sg_profile_enable", _I, [_I]),
     ("sg_profile_read", _I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     ("sg_profile_reset", _I, []),
+    ("sg_launch_count", ctypes.c_longlong, []),
 ]
 
 _lib = None
@@ -264,3 +265,8 @@ def profile_read(kernel_id):
     cnt = ctypes.c_longlong(0)
     _check(lib().sg_profile_read(int(kernel_id), ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().sg_launch_count())

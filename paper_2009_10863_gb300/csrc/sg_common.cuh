@@ -21,8 +21,11 @@ int sg_fail(int code, const std::string& msg);
       return sg_fail(SG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+void sg_count_launch();
+
 #define SG_LAUNCH_CHECK(name)                                                    \
   do {                                                                          \
+    sg_count_launch();                                                           \
     cudaError_t e_ = cudaGetLastError();                                         \
     if (e_ != cudaSuccess)                                                       \
       return sg_fail(SG_ERR_CUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e_)); \
@@ -76,6 +79,7 @@ struct SemGeom {
   int nx, ny, nz;          // global nodes per axis (p*e + 1)
   int ex, ey, ez, p;
   double cm;               // lambda * hx hy hz / 8
+  double adir[3];          // direction factors J (2/h_d)^2 = (hx hy hz / h_d^2) / 2
   double C[3][SG_PMAX + 1][SG_PMAX + 1];  // per direction x, y, z
   double wl[SG_PMAX + 1];  // assembled 1D mass by local index (wl[0] = w0 + wp)
   double dg[3][SG_PMAX + 1];              // diagonal coefficient by local index

@@ -1,4 +1,5 @@
 // sg_op.cu -- operator handle, sg_sem_apply, diagonal, errors and kernel timing.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -19,6 +20,10 @@ void sg_set_error(const std::string& msg) { g_err = msg; }
 int sg_fail(int code, const std::string& msg) { g_err = msg; return code; }
 extern "C" const char* sg_last_error(void) { return g_err.c_str(); }
 extern "C" int sg_version(void) { return 1; }
+
+static std::atomic<long long> g_launches{0};
+void sg_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" long long sg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int sg_num_sms() {
   static int n = 0;
@@ -127,6 +132,7 @@ static void build_geom(sg_op_s* op) {
     for (int a = 1; a < p; ++a) g.dg[d][a] = adir[d] * K[a * n1 + a] / w[a];
   }
   for (int a = 0; a <= p; ++a) g.wl[a] = (a == 0) ? wsh : w[a];
+  for (int d = 0; d < 3; ++d) g.adir[d] = adir[d];
   g.cm = op->lambda * hx * hy * hz / 8.0;
 }
 

@@ -1,27 +1,37 @@
 // sg_sem_kernel.cuh -- the tiled matrix-free SEM operator kernel (Sec. 5.1).
 //
-// Node-centric form of the assembled affine-box operator (see SemGeom):
-//   (A u)_ijk = W_i W_j W_k [ (C_x u)_i + (C_y u)_j + (C_z u)_k + c_m u_ijk ].
-// Row a of C_dir (a = local index of the node in its element) touches only
-// the nodes of the node's element along that direction, plus, for a = 0 (a
-// node shared by elements e-1 and e), those of element e-1.  Each output node
-// is therefore computed exactly once, without atomics or a scatter pass.
+// Form of the operator (see SemGeom): on the affine box the assembled operator
+// is a Kronecker sum of assembled 1D operators,
+//   (A u)_ijk = W_i W_j W_k [ (C_x u)_i + (C_y u)_j + (C_z u)_k + c_m u_ijk ],
+// where row a of C (a = local index of the node in its element) combines the
+// p+1 nodes of the node's element along that direction, and a shared node
+// (a = 0) also row p of C on the element before it.
 //
-// Tiling: a CTA owns an element-aligned tile of TX x TY nodes in x,y (one
-// thread per (x,y) column) and marches through ZL element layers in z.  For
-// each layer the p+1 planes z = e p .. e p + p are held in shared memory,
-// padded by p nodes below and 1 node above in x and y; the top plane of a
-// layer is reused as the bottom plane of the next.  The z-contraction runs in
-// registers on the thread's own column; the x- and y-contractions read the
-// padded planes.  Nodes with local index p-1... 0 are owned; the upper
-// boundary faces (index n-1) are Dirichlet and are written as 0 separately.
+// Element-line contractions.  Per direction the kernel applies the (p+1)x(p+1)
+// matrix C to each element line (the sum-factorised tensor contraction of the
+// paper's local operator).  C is centrosymmetric (C[p-a][p-l] = C[a][l]), so
+// each line uses the even-odd split: s_l = u_l + u_{p-l}, d_l = u_l - u_{p-l},
+// o_a = E_a + O_a, o_{p-a} = E_a - O_a with two half-size products -- about
+// 3/4 of the multiply-adds of the plain product, and no divergent branches.
+// The contribution of the element before a shared node (row p of C on its
+// line) is added by the line that owns the node, so every output node is
+// written exactly once, without atomics or a scatter pass.
+//
+// Tiling.  A CTA owns TEX x TEY elements in x,y (TX x TY nodes, one thread per
+// (x,y) column) and marches through ZL element layers in z.  For each layer the
+// p+1 planes z = e p .. e p + p sit in shared memory, padded by p nodes below
+// and 1 above in x and y (the top plane is reused as the next layer's bottom).
+//   z: each thread contracts its own column in registers; the top output of a
+//      layer is carried to the next layer's bottom node;
+//   x: item (plane c, row y, element) -> p outputs written to a work buffer;
+//   y: item (plane c, column x, element) -> p outputs written to the buffer;
+// the thread then adds its column's x and y results, the mass term and the
+// weights, and stores.  The upper Dirichlet faces (index n-1) are written 0.
 //
 // MODE 0: out = A x.
-// MODE 1: PCG step (Sec. 5.3): p_new = z + beta p_old (p_new = z on the first
-//         iteration), out2 = p_new, out = q = A p_new, partial p_new . q;
-//         the last CTA forms alpha = (r.z) / (p.q).
-// MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A), partials
-//         r.r, r.z, b.b; the last CTA stores them (PCG start / true residual).
+// MODE 1: PCG step (Sec. 5.3): p_new = z + beta p_old (p_new = z first), staged
+//         on load; out2 = p_new, out = q = A p_new; p_new . q -> alpha.
+// MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A); r.r, r.z, b.b.
 #pragma once
 #include "sg_common.cuh"
 
@@ -33,7 +43,7 @@ struct PcgState {
   int maxit, criterion;
   double tol;
   unsigned int counter[4];
-  int diag_tag;            // nonzero once inverse diagonal is in the workspace
+  int diag_tag;
   int pad[7];
 };
 
@@ -41,12 +51,14 @@ enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXIT = 2, PCG_BREAKDOWN = 3 };
 
 template <int P>
 struct SemTile {
-  static constexpr int TEX = ((28 + P / 2) / P) > 0 ? ((28 + P / 2) / P) : 1;
-  static constexpr int TEY = ((14 + P / 2) / P) > 0 ? ((14 + P / 2) / P) : 1;
+  static constexpr int TEX = (P <= 2) ? 8 : (P <= 4 ? 4 : 2);
+  static constexpr int TEY = (P <= 2) ? 4 : 2;
   static constexpr int TX = TEX * P, TY = TEY * P;
   static constexpr int PX = TX + P + 1, PY = TY + P + 1, NPL = P + 1;
-  static constexpr int CS = P + 2;  // padded row stride of the coefficient tables
   static constexpr int NTHREADS = TX * TY;
+  static constexpr int N = P + 1, H = (P + 1) / 2;
+  static constexpr bool MID = ((P + 1) % 2) == 1;
+  static constexpr int HE = H + (MID ? 1 : 0);   // even-part outputs (incl. middle)
 };
 
 template <typename T>
@@ -62,19 +74,98 @@ struct SemArgs {
   int final_pass; // MODE 2: 1 = true-residual check (store rr_true only)
 };
 
+// Even-odd coefficient tables of one direction (scaled by the direction factor).
 template <typename T, int P>
-__device__ __forceinline__ bool interior_node(const SemGeom& g, int gx, int gy, int gz) {
-  return gx > 0 && gy > 0 && gz > 0 && gx < g.nx - 1 && gy < g.ny - 1 && gz < g.nz - 1;
+struct EOTab {
+  using TL = SemTile<P>;
+  T ce[TL::HE][TL::H];   // (C[a][l] + C[a][p-l]) / 2, a < H (+ middle row)
+  T co[TL::H][TL::H];    // (C[a][l] - C[a][p-l]) / 2, a < H
+  T cm[TL::HE];          // C[a][mid] (odd line length only)
+  T crow[P + 1];         // row p of C: contribution to the next element's node 0
+};
+
+// o[0..P] = C u for one element line (even-odd), coefficients from table t.
+template <typename T, int P>
+__device__ __forceinline__ void line_eo(const T (&u)[P + 1], const EOTab<T, P>& t, T (&o)[P + 1]) {
+  using TL = SemTile<P>;
+  constexpr int H = TL::H;
+  T s[H], d[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) { s[l] = u[l] + u[P - l]; d[l] = u[l] - u[P - l]; }
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    T e = t.ce[a][0] * s[0];
+    T od = t.co[a][0] * d[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) { e += t.ce[a][l] * s[l]; od += t.co[a][l] * d[l]; }
+    if (TL::MID) e += t.cm[a] * u[P / 2];
+    o[a] = e + od;
+    o[P - a] = e - od;
+  }
+  if (TL::MID) {
+    T e = t.cm[H] * u[P / 2];
+#pragma unroll
+    for (int l = 0; l < H; ++l) e += t.ce[H][l] * s[l];
+    o[P / 2] = e;
+  }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ T row_dot(const T (&u)[P + 1], const EOTab<T, P>& t) {
+  T r = t.crow[0] * u[0];
+#pragma unroll
+  for (int l = 1; l <= P; ++l) r += t.crow[l] * u[l];
+  return r;
+}
+
+// Tables of direction d, multiplied by ``mul`` (1 for the scaled tables; 1/a_d
+// for the unscaled register copy used by the FP32 kernel).
+template <typename T, int P>
+__host__ __device__ inline void build_eotab(const SemGeom& g, int d, double mul, EOTab<T, P>& t) {
+  using TL = SemTile<P>;
+  constexpr int H = TL::H;
+  for (int a = 0; a < TL::HE; ++a) {
+    const int aa = (a < H) ? a : P / 2;
+    for (int l = 0; l < H; ++l) {
+      t.ce[a][l] = (T)(mul * 0.5 * (g.C[d][aa][l] + g.C[d][aa][P - l]));
+      if (a < H) t.co[a][l] = (T)(mul * 0.5 * (g.C[d][aa][l] - g.C[d][aa][P - l]));
+    }
+    t.cm[a] = TL::MID ? (T)(mul * g.C[d][aa][P / 2]) : (T)0;
+  }
+  for (int l = 0; l <= P; ++l) t.crow[l] = (T)(mul * g.C[d][P][l]);
+}
+
+// One direction's line product: FP64 reads the scaled table of the direction
+// from shared memory; FP32 uses the unscaled register table times a_d.
+template <typename T, int P, bool CREG>
+__device__ __forceinline__ void dir_line(const T (&u)[P + 1], T (&o)[P + 1], const EOTab<T, P>& st,
+                                         const EOTab<T, P>& rt, T scale) {
+  if constexpr (CREG) {
+    line_eo<T, P>(u, rt, o);
+#pragma unroll
+    for (int c = 0; c <= P; ++c) o[c] *= scale;
+  } else {
+    line_eo<T, P>(u, st, o);
+  }
+}
+
+template <typename T, int P, bool CREG>
+__device__ __forceinline__ T dir_row(const T (&u)[P + 1], const EOTab<T, P>& st, const EOTab<T, P>& rt, T scale) {
+  if constexpr (CREG) return scale * row_dot<T, P>(u, rt);
+  else return row_dot<T, P>(u, st);
 }
 
 template <typename T, int P, int MODE>
 __global__ void __launch_bounds__(SemTile<P>::NTHREADS)
 k_sem(const SemGeom g, const SemArgs<T> a) {
   using TL = SemTile<P>;
-  constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL, CS = TL::CS;
+  constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL;
+  constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
+  constexpr bool CREG = sizeof(T) == 4;   // FP32: coefficients in registers
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);                     // NPL planes of PY x PX
-  __shared__ T sC[3][P + 1][CS];
+  T* S = reinterpret_cast<T*>(smem_raw);               // NPL planes of PY x PX
+  T* Wb = S + (size_t)NPL * PY * PX;                   // P planes of TY x TX (x / y results)
+  __shared__ EOTab<T, P> sTab[4];
   __shared__ T sW[P + 1];
   __shared__ double sred[32 * 3];
   __shared__ int s_skip;
@@ -83,20 +174,22 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  if (MODE == 1) {
-    if (tid == 0) {
+  if (tid == 0) {
+    if (MODE == 1) {
       s_skip = a.st->done;
       s_beta = (T)a.st->beta;
       s_first = a.st->first;
     }
   }
-  for (int i = tid; i < 3 * (P + 1) * (P + 1); i += TL::NTHREADS) {
-    int d = i / ((P + 1) * (P + 1)), r = (i / (P + 1)) % (P + 1), c = i % (P + 1);
-    sC[d][r][c] = (T)g.C[d][r][c];
-  }
-  for (int i = tid; i <= P; i += TL::NTHREADS) sW[i] = (T)g.wl[i];
+  if (tid < 3) build_eotab<T, P>(g, tid, 1.0, sTab[tid]);
+  if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
+  if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
   if (MODE == 1 && s_skip) return;
+
+  EOTab<T, P> rt;                 // FP32: register copy of the unscaled table
+  if constexpr (CREG) rt = sTab[3];
+  const T sx = (T)g.adir[0], sy = (T)g.adir[1], sz = (T)g.adir[2];
 
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int e0 = blockIdx.z * a.zl;
@@ -109,7 +202,6 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   const T cm = (T)g.cm;
   const size_t nxy = (size_t)g.nx * g.ny;
 
-  // value of the operand at a global point (0 outside the interior)
   auto operand = [&](int px, int py, int pz) -> T {
     if (px <= 0 || py <= 0 || pz <= 0 || px >= g.nx - 1 || py >= g.ny - 1 || pz >= g.nz - 1)
       return (T)0;
@@ -121,81 +213,100 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     return a.x[idx];
   };
 
-  // z-carry from the element below the chunk: its line's contribution to plane e0*P
+  // z-carry from the element layer below the chunk (row p on its line)
   T carry = (T)0;
   if (e0 > 0 && col_int) {
     T ub[P + 1];
 #pragma unroll
     for (int l = 0; l <= P; ++l) ub[l] = operand(gx, gy, (e0 - 1) * P + l);
-#pragma unroll
-    for (int l = 0; l <= P; ++l) carry += sC[2][P][l] * ub[l];
+    carry = dir_row<T, P, CREG>(ub, sTab[2], rt, sz);
   }
+
+  // x / y item coordinates (one item per thread per phase)
+  const int xi_e = tid % TEX, xi_r = (tid / TEX) % TY, xi_c = tid / (TEX * TY);
+  const int yi_e = tid % TEY, yi_r = (tid / TEY) % TX, yi_c = tid / (TEY * TX);
 
   double acc_red[3] = {0.0, 0.0, 0.0};
 
   for (int e = e0; e < e1; ++e) {
-    // ---- stage planes e*P .. e*P + P (the first plane is kept from the last layer)
+    // ---- stage planes e*P .. e*P + P (the bottom plane is kept from the last layer)
     __syncthreads();
     const int pl0 = (e == e0) ? 0 : 1;
     for (int pl = pl0; pl <= P; ++pl) {
       const int gz = e * P + pl;
       T* plane = S + (size_t)(gz % NPL) * PY * PX;
-      for (int i = tid; i < PY * PX; i += TL::NTHREADS) {
+      for (int i = tid; i < PY * PX; i += NT) {
         int py = i / PX, px = i - py * PX;
         plane[i] = operand(x0 - P + px, y0 - P + py, gz);
       }
     }
     __syncthreads();
 
-    T u[P + 1];
+    // ---- z: own column in registers
+    T u[P + 1], acc[P];
 #pragma unroll
     for (int l = 0; l <= P; ++l)
       u[l] = S[(size_t)((e * P + l) % NPL) * PY * PX + (ty + P) * PX + (tx + P)];
+    {
+      T o[P + 1];
+      dir_line<T, P, CREG>(u, o, sTab[2], rt, sz);
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc[c] = o[c] + cm * u[c];
+      acc[0] += carry;
+      carry = o[P];
+    }
 
+    // ---- x: item (plane c, row, element) -> work buffer
+    {
+      const T* row = S + (size_t)((e * P + xi_c) % NPL) * PY * PX + (xi_r + P) * PX + xi_e * P;
+      T ul[P + 1], ue[P + 1], o[P + 1];
+#pragma unroll
+      for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
+      dir_line<T, P, CREG>(ue, o, sTab[0], rt, sx);
+      o[0] += dir_row<T, P, CREG>(ul, sTab[0], rt, sx);
+      T* w = Wb + ((size_t)xi_c * TY + xi_r) * TX + xi_e * P;
+#pragma unroll
+      for (int c = 0; c < P; ++c) w[c] = o[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
+    __syncthreads();
+
+    // ---- y: item (plane c, column, element) -> work buffer
+    {
+      const T* col = S + (size_t)((e * P + yi_c) % NPL) * PY * PX + (size_t)(yi_e * P) * PX + (yi_r + P);
+      T ul[P + 1], ue[P + 1], o[P + 1];
+#pragma unroll
+      for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
+      dir_line<T, P, CREG>(ue, o, sTab[1], rt, sy);
+      o[0] += dir_row<T, P, CREG>(ul, sTab[1], rt, sy);
+      T* w = Wb + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
+#pragma unroll
+      for (int c = 0; c < P; ++c) w[(size_t)c * TX] = o[c];
+    }
+    __syncthreads();
+
+    // ---- combine, weights, store
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
-      const T* plane = S + (size_t)(gz % NPL) * PY * PX;
-      // z-direction: own column, element e (+ carry from element e-1 at c = 0)
-      T acc = cm * u[c];
-#pragma unroll
-      for (int l = 0; l <= P; ++l) acc += sC[2][c][l] * u[l];
-      if (c == 0) acc += carry;
-      // x-direction
-      {
-        const T* row = plane + (ty + P) * PX + (tx - ia + P);
-#pragma unroll
-        for (int l = 0; l <= P; ++l) acc += sC[0][ia][l] * row[l];
-        if (ia == 0) {
-#pragma unroll
-          for (int l = 0; l <= P; ++l) acc += sC[0][P][l] * row[l - P];
-        }
-      }
-      // y-direction
-      {
-        const T* colp = plane + (ty - ib + P) * PX + (tx + P);
-#pragma unroll
-        for (int l = 0; l <= P; ++l) acc += sC[1][ib][l] * colp[l * PX];
-        if (ib == 0) {
-#pragma unroll
-          for (int l = 0; l <= P; ++l) acc += sC[1][P][l] * colp[(l - P) * PX];
-        }
-      }
+      const T v = acc[c] + Wb[((size_t)c * TY + ty) * TX + tx];
       const bool inside = col_int && gz > 0;
-      T yv = inside ? (wxy * sW[c]) * acc : (T)0;
+      const T yv = inside ? (wxy * sW[c]) * v : (T)0;
       if (col_in) {
         size_t idx = (size_t)gx + (size_t)g.nx * gy + nxy * gz;
         if (MODE == 0) {
           a.out[idx] = yv;
         } else if (MODE == 1) {
-          T pv = u[c];
+          const T pv = u[c];
           a.out[idx] = yv;
           a.out2[idx] = pv;
           acc_red[0] += (double)pv * (double)yv;
         } else {
-          T bv = inside ? a.aux[idx] : (T)0;
-          T rv = inside ? bv - yv : (T)0;
-          T zv = rv * a.invd[idx];
+          const T bv = inside ? a.aux[idx] : (T)0;
+          const T rv = inside ? bv - yv : (T)0;
+          const T zv = rv * a.invd[idx];
           a.out[idx] = rv;
           if (!a.final_pass) a.out2[idx] = zv;
           acc_red[0] += (double)rv * (double)rv;
@@ -204,22 +315,18 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
         }
       }
     }
-    // carry for the next layer: element e's line contribution to plane (e+1)P
-    carry = (T)0;
-#pragma unroll
-    for (int l = 0; l <= P; ++l) carry += sC[2][P][l] * u[l];
   }
 
   // ---- upper Dirichlet faces (index n-1) inside this CTA's region: write 0
   {
     const bool lastx = (x0 + TX >= g.nx - 1), lasty = (y0 + TY >= g.ny - 1);
     const bool lastz = (e1 == g.ez);
-    const int xe = lastx ? g.nx : x0 + TX, ye = lasty ? g.ny : y0 + TY;
-    const int z0 = e0 * P, ze = lastz ? g.nz : e1 * P;
-    const int wx = xe - x0, wy = ye - y0, wz = ze - z0;
-    const int total = wx * wy * wz;
     if (lastx || lasty || lastz) {
-      for (int i = tid; i < total; i += TL::NTHREADS) {
+      const int xe = lastx ? g.nx : x0 + TX, ye = lasty ? g.ny : y0 + TY;
+      const int z0 = e0 * P, ze = lastz ? g.nz : e1 * P;
+      const int wx = xe - x0, wy = ye - y0, wz = ze - z0;
+      const int total = wx * wy * wz;
+      for (int i = tid; i < total; i += NT) {
         int lx = i % wx, ly = (i / wx) % wy, lz = i / (wx * wy);
         int px = x0 + lx, py = y0 + ly, pz = z0 + lz;
         if (px == g.nx - 1 || py == g.ny - 1 || pz == g.nz - 1) {
