@@ -93,6 +93,7 @@ struct sg_op_s {
   double nodes[SG_PMAX + 1], weights[SG_PMAX + 1];
   FastDiv div_nx, div_nxy;
   int device;
+  unsigned long long uid;   // unique per created operator (never reused)
 };
 
 // ---------------------------------------------------------------- reductions

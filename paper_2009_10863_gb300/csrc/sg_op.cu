@@ -164,6 +164,8 @@ extern "C" int sg_op_create(sg_op_t* out, int ex, int ey, int ez, int p, double 
     }
   }
   cudaGetDevice(&op->device);
+  static std::atomic<unsigned long long> next_uid{1};
+  op->uid = next_uid.fetch_add(1);
   *out = op;
   return SG_OK;
 }

@@ -62,9 +62,9 @@ PcgLayout layout_for(sg_op_t op) {
   return L;
 }
 
-// which operator last wrote 1/diag into a workspace (host-side bookkeeping)
+// which operator (by unique id) last wrote 1/diag into a workspace
 std::mutex g_ws_mu;
-std::map<void*, const void*> g_ws_owner;
+std::map<void*, unsigned long long> g_ws_owner;
 
 struct PollBuf { int iter, done, status, pad; };
 
@@ -186,10 +186,10 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   {
     std::lock_guard<std::mutex> lk(g_ws_mu);
     auto it = g_ws_owner.find(ws);
-    if (it == g_ws_owner.end() || it->second != (const void*)op) {
+    if (it == g_ws_owner.end() || it->second != op->uid) {
       int rc = sg_op_diag_launch(op, invd, 1, s);
       if (rc) return rc;
-      g_ws_owner[ws] = op;
+      g_ws_owner[ws] = op->uid;
     }
   }
   k_mask_faces<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz);
