@@ -7,12 +7,7 @@
 // The host launches a chunk of iterations and then reads the done flag once;
 // kernels after convergence return immediately.  Vector traffic: 12 n words
 // per iteration (4 in the operator kernel, 8 in the update).
-#include <map>
-#include <mutex>
-
 #include "sg_sem_launch.cuh"
-
-int sg_op_diag_launch(sg_op_t op, void* out, int inverse, cudaStream_t s);
 
 namespace {
 
@@ -62,9 +57,10 @@ PcgLayout layout_for(sg_op_t op) {
   return L;
 }
 
-// which operator (by unique id) last wrote 1/diag into a workspace
-std::mutex g_ws_mu;
-std::map<void*, unsigned long long> g_ws_owner;
+// Tag of the inverse diagonal held in a workspace: derived from the operator's
+// unique id, checked on the device so a workspace whose contents changed (or a
+// fresh one) always gets the diagonal recomputed.
+inline unsigned long long diag_tag(sg_op_t op) { return 0x5347494e56444941ull ^ (op->uid * 0x9e3779b97f4a7c15ull); }
 
 struct PollBuf { int iter, done, status, pad; };
 
@@ -89,6 +85,29 @@ __global__ void k_mask_faces(T* v, int nx, int ny, int nz) {
     v[(size_t)zi * nxy + (size_t)yi * nx] = (T)0;
     v[(size_t)zi * nxy + (size_t)yi * nx + nx - 1] = (T)0;
   }
+}
+
+// 1/diag(A) into out unless the workspace already holds it for this operator.
+template <typename T>
+__global__ void k_inv_diag_cached(const SemGeom g, FastDiv dnx, FastDiv dnxy, int n, T* out,
+                                  const PcgState* st, unsigned long long tag) {
+  if (st->diag_tag == tag) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t k = dnxy.div((uint32_t)i);
+    uint32_t rem = (uint32_t)i - k * dnxy.d;
+    uint32_t j = dnx.div(rem);
+    uint32_t ii = rem - j * dnx.d;
+    double v = 1.0;
+    if (ii > 0 && j > 0 && k > 0 && (int)ii < g.nx - 1 && (int)j < g.ny - 1 && (int)k < g.nz - 1) {
+      int a = ii % g.p, b = j % g.p, c = k % g.p;
+      v = g.wl[a] * g.wl[b] * g.wl[c] * (g.dg[0][a] + g.dg[1][b] + g.dg[2][c] + g.cm);
+    }
+    out[i] = (T)(1.0 / v);
+  }
+}
+
+__global__ void k_set_diag_tag(PcgState* st, unsigned long long tag) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->diag_tag = tag;
 }
 
 __global__ void k_pcg_setup(PcgState* st, double tol, int maxit, int criterion) {
@@ -184,13 +203,13 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   const SemGeom& g = op->g;
 
   {
-    std::lock_guard<std::mutex> lk(g_ws_mu);
-    auto it = g_ws_owner.find(ws);
-    if (it == g_ws_owner.end() || it->second != op->uid) {
-      int rc = sg_op_diag_launch(op, invd, 1, s);
-      if (rc) return rc;
-      g_ws_owner[ws] = op->uid;
-    }
+    const unsigned long long tag = diag_tag(op);
+    int blocks = (n + 255) / 256;
+    if (blocks > 16 * sg_num_sms()) blocks = 16 * sg_num_sms();
+    k_inv_diag_cached<T><<<blocks, 256, 0, s>>>(g, op->div_nx, op->div_nxy, n, invd, st, tag);
+    SG_LAUNCH_CHECK("k_inv_diag_cached");
+    k_set_diag_tag<<<1, 32, 0, s>>>(st, tag);
+    SG_LAUNCH_CHECK("k_set_diag_tag");
   }
   k_mask_faces<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz);
   SG_LAUNCH_CHECK("k_mask_faces");
@@ -278,3 +297,4 @@ extern "C" int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int 
   return pcg_run<float>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit,
                         criterion, ws, L, iters, relres, s);
 }
+

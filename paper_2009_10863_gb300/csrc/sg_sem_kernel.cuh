@@ -43,8 +43,8 @@ struct PcgState {
   int maxit, criterion;
   double tol;
   unsigned int counter[4];
-  int diag_tag;
-  int pad[7];
+  unsigned long long diag_tag;   // operator tag of the 1/diag(A) held in the workspace
+  int pad[6];
 };
 
 enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXIT = 2, PCG_BREAKDOWN = 3 };
