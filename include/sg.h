@@ -116,6 +116,33 @@ int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int 
                  void* workspace, int* iters, double* relres, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free PCG.  The paper has no counterpart: this entry point is for
+ * callers that cannot allocate device memory -- code whose device memory is
+ * owned by a host framework that hands out no more, or a time-critical loop
+ * that must not enter the driver's allocation path.  It runs the same solver
+ * as sg_pcg_solve, but its scratch (the PCG vectors, reduction partials and
+ * state) is a file-scope static __device__ array of SG_NOALLOC_SCRATCH_BYTES,
+ * held by every GPU that loads the library until the process exits.  It calls
+ * no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine; it polls
+ * convergence through pageable host memory, and kernel timing is off for it.
+ *  - Operators with more than SG_NOALLOC_MAX_NODES nodes are rejected with
+ *    SG_ERR_INVALID (message via sg_last_error()).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on that device.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; the call resets what must start at zero itself.  Calls whose
+ *    work overlaps on the GPU (other streams, other host threads) race on the
+ *    array: serialise them.
+ * Arguments, outputs and return codes are those of sg_pcg_solve without the
+ * workspace.  Synchronises with ``stream``.
+ * ------------------------------------------------------------------------ */
+#define SG_NOALLOC_MAX_NODES 131072
+#define SG_NOALLOC_SCRATCH_BYTES (6815744) /* 6.5 MiB */
+int sg_pcg_solve_noalloc(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
+                         int* iters, double* relres, void* stream);
+
+/* ------------------------------------------------------------------------
  * Initial guesses (Sec. 2-3).  A guess handle keeps the history spaces in
  * the caller's workspace: for EXTRAP/SPEXTRAP/LAST a ring of s solutions
  * (Sec. 3, Eq. ExtrapExpn); for PROJ_QR/PROJ_CLASSIC the right-hand-side

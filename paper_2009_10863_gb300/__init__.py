@@ -52,6 +52,7 @@ SIGNATURES = [
     ("sg_profile_read", _I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     ("sg_profile_reset", _I, []),
     ("sg_launch_count", ctypes.c_longlong, []),
+    ("sg_pcg_solve_noalloc", _I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
 ]
 
 _lib = None

@@ -7,6 +7,9 @@
 // The host launches a chunk of iterations and then reads the done flag once;
 // kernels after convergence return immediately.  Vector traffic: 12 n words
 // per iteration (4 in the operator kernel, 8 in the update).
+#include <mutex>
+#include <string>
+
 #include "sg_sem_launch.cuh"
 
 namespace {
@@ -189,7 +192,14 @@ k_pcg_update(T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r, cons
   }
 }
 
-template <typename T>
+// Library-side kernel timing around a launch, compiled out for the
+// allocation-free entry point (event creation allocates).
+template <bool ON>
+struct MaybeProf { MaybeProf(int, cudaStream_t) {} };
+template <>
+struct MaybeProf<true> { ProfScope ps; MaybeProf(int id, cudaStream_t s) : ps(id, s) {} };
+
+template <typename T, bool NOALLOC = false>
 static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion,
                    unsigned char* ws, const PcgLayout& L, int* iters, double* relres, cudaStream_t s) {
   PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
@@ -223,8 +233,13 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
     if (rc) return rc;
   }
   const int ub = update_blocks(op->n, Vec<T>::W);
-  static thread_local PollBuf* poll = nullptr;
-  if (!poll) SG_CUDA_TRY(cudaHostAlloc((void**)&poll, sizeof(PollBuf), cudaHostAllocDefault));
+  PollBuf local_poll{};      // pageable host memory: no pinned allocation
+  PollBuf* poll = &local_poll;
+  if constexpr (!NOALLOC) {
+    static thread_local PollBuf* pinned = nullptr;
+    if (!pinned) SG_CUDA_TRY(cudaHostAlloc((void**)&pinned, sizeof(PollBuf), cudaHostAllocDefault));
+    poll = pinned;
+  }
   int launched = 0, chunk = 4;
   while (true) {
     SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
@@ -237,7 +252,7 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
       T* pnew = pb[it & 1];
       const T* pold = pb[(it + 1) & 1];
       {
-        ProfScope ps(PROF_PCG_APPLY, s);
+        MaybeProf<!NOALLOC> ps(PROF_PCG_APPLY, s);
         SemArgs<T> a{};
         a.x = z; a.aux = pold; a.out = q; a.out2 = pnew;
         a.partials = partials; a.st = st;
@@ -245,7 +260,7 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
         if (rc) return rc;
       }
       {
-        ProfScope ps(PROF_PCG_UPDATE, s);
+        MaybeProf<!NOALLOC> ps(PROF_PCG_UPDATE, s);
         k_pcg_update<T><<<ub, 256, 0, s>>>(x, pnew, r, q, invd, z, n, st, partials);
         SG_LAUNCH_CHECK("k_pcg_update");
       }
@@ -298,3 +313,57 @@ extern "C" int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int 
                         criterion, ws, L, iters, relres, s);
 }
 
+// ---------------------------------------------------------------- allocation-free PCG
+// Scratch for sg_pcg_solve_noalloc: a file-scope device array, so the call needs
+// no workspace from the caller and allocates nothing.  Every device that loads
+// the library holds these SG_NOALLOC_SCRATCH_BYTES until the process exits.
+static __device__ __align__(256) unsigned char g_pcg_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};   // device address of g_pcg_scratch, per device
+}
+
+extern "C" int sg_pcg_solve_noalloc(sg_op_t op, const void* b, void* x, double tol, int maxit,
+                                    int criterion, int* iters, double* relres, void* stream) {
+  if (!op || !b || !x) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: NULL argument");
+  if (op->n > SG_NOALLOC_MAX_NODES)
+    return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: operator has " + std::to_string(op->n) +
+                                   " nodes, above the maximum of " + std::to_string(SG_NOALLOC_MAX_NODES));
+  if (!(tol > 0.0)) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: tol must be > 0");
+  if (maxit < 0) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: maxit must be >= 0");
+  if (criterion < 0 || criterion > 2) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: unknown criterion");
+  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: vectors must be 16-byte aligned");
+  if (b == x) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: b and x must not alias");
+  PcgLayout L = layout_for(op);
+  if (L.total > SG_NOALLOC_SCRATCH_BYTES)
+    return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: scratch of " + std::to_string(L.total) +
+                                   " bytes needed, above the static " + std::to_string((size_t)SG_NOALLOC_SCRATCH_BYTES));
+  int dev = 0;
+  SG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: device index out of range");
+  void* ptr = nullptr;
+  {
+    // set-up, once per device with that device current: the host-side name of
+    // the array is not a device address, so look the address up.
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+      if (e != cudaSuccess || !p)
+        return sg_fail(SG_ERR_CUDA, std::string("pcg_solve_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_scratch_addr[dev] = p;
+    }
+    ptr = g_scratch_addr[dev];
+  }
+  // The PCG state (reduction counters included) is reset on the stream by
+  // k_pcg_setup, and the cached 1/diag(A) is revalidated by its device tag, so
+  // the array's leftover contents from an earlier call are harmless.
+  unsigned char* ws = static_cast<unsigned char*>(ptr);
+  cudaStream_t s = as_stream(stream);
+  if (op->dtype == SG_F64)
+    return pcg_run<double, true>(op, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit,
+                                 criterion, ws, L, iters, relres, s);
+  return pcg_run<float, true>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit,
+                              criterion, ws, L, iters, relres, s);
+}
