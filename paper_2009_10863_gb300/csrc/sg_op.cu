@@ -101,10 +101,12 @@ extern "C" int sg_profile_read(int id, double* total_ms, long long* launches) {
 int sg_sem_layers(const SemGeom& g, int tex, int tey, int override_zl) {
   if (override_zl > 0) return override_zl < g.ez ? override_zl : g.ez;
   const long nxy = (long)((g.ex + tex - 1) / tex) * ((g.ey + tey - 1) / tey);
-  const long want = 4L * sg_num_sms();           // CTAs to aim for
+  const long want = 8L * sg_num_sms();           // CTAs to aim for (several waves)
   long zl = (nxy * g.ez) / want;
   if (zl < 1) zl = 1;
   if (zl > g.ez) zl = g.ez;
+  const long nchunks = (g.ez + zl - 1) / zl;     // balance: chunks differ by <= 1 layer
+  zl = (g.ez + nchunks - 1) / nchunks;
   return (int)zl;
 }
 

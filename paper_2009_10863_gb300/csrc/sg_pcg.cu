@@ -1,12 +1,16 @@
 // sg_pcg.cu -- fused Jacobi-PCG (Sec. 5.3) with the stopping rules of Sec. 6.4.
 //
 // Per iteration two launches, all scalars kept on the device:
-//   k_sem<MODE 1>:  p = z + beta p (p = z first), q = A p, p.q -> alpha = (r.z)/(p.q)
+//   k_sem<MODE 1>:  w = A z; p = z + beta p, q = w + beta q (= A p by
+//                   linearity; p = z, q = w first); p.q -> alpha = (r.z)/(p.q)
 //   k_pcg_update:   x += alpha p, r -= alpha q, z = r / diag(A), r.r, r.z
 //                   -> convergence test on ||r||, beta = (r.z)_new / (r.z)
-// The host launches a chunk of iterations and then reads the done flag once;
-// kernels after convergence return immediately.  Vector traffic: 12 n words
-// per iteration (4 in the operator kernel, 8 in the update).
+// Applying A to z (which the update kernel has just written) instead of to the
+// new p lets the operator stage a plain copy of one vector; p and q are then
+// formed for owned nodes only.  The host launches a chunk of iterations and
+// then reads the done flag once; kernels after convergence return at once.
+// Vector traffic: 13 n words per iteration (5 in the operator kernel, 8 in
+// the update).
 #include <mutex>
 #include <string>
 
@@ -18,7 +22,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct PcgLayout {
-  size_t state, partials, r, z, pa, pb, q, invd, total;
+  size_t state, partials, r, z, p, q, invd, total;
   int max_blocks;
 };
 
@@ -52,8 +56,7 @@ PcgLayout layout_for(sg_op_t op) {
   L.partials = off; off += align_up(sizeof(double) * 4 * (size_t)L.max_blocks);
   L.r = off; off += vb;
   L.z = off; off += vb;
-  L.pa = off; off += vb;
-  L.pb = off; off += vb;
+  L.p = off; off += vb;
   L.q = off; off += vb;
   L.invd = off; off += vb;
   L.total = off;
@@ -206,7 +209,7 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   double* partials = reinterpret_cast<double*>(ws + L.partials);
   T* r = reinterpret_cast<T*>(ws + L.r);
   T* z = reinterpret_cast<T*>(ws + L.z);
-  T* pb[2] = {reinterpret_cast<T*>(ws + L.pa), reinterpret_cast<T*>(ws + L.pb)};
+  T* p = reinterpret_cast<T*>(ws + L.p);
   T* q = reinterpret_cast<T*>(ws + L.q);
   T* invd = reinterpret_cast<T*>(ws + L.invd);
   const int n = (int)op->n;
@@ -248,20 +251,17 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
     if (launched >= maxit) break;   // defensive; the device sets done at maxit
     const int k = (chunk < maxit - launched) ? chunk : (maxit - launched);
     for (int i = 0; i < k; ++i) {
-      const int it = launched + i;
-      T* pnew = pb[it & 1];
-      const T* pold = pb[(it + 1) & 1];
       {
         MaybeProf<!NOALLOC> ps(PROF_PCG_APPLY, s);
         SemArgs<T> a{};
-        a.x = z; a.aux = pold; a.out = q; a.out2 = pnew;
+        a.x = z; a.out = q; a.out2 = p;
         a.partials = partials; a.st = st;
         int rc = sg_sem_launch<T, 1>(g, a, s, 0);
         if (rc) return rc;
       }
       {
         MaybeProf<!NOALLOC> ps(PROF_PCG_UPDATE, s);
-        k_pcg_update<T><<<ub, 256, 0, s>>>(x, pnew, r, q, invd, z, n, st, partials);
+        k_pcg_update<T><<<ub, 256, 0, s>>>(x, p, r, q, invd, z, n, st, partials);
         SG_LAUNCH_CHECK("k_pcg_update");
       }
     }

@@ -21,6 +21,8 @@
 // (x,y) column) and marches through ZL element layers in z.  For each layer the
 // p+1 planes z = e p .. e p + p sit in shared memory, padded by p nodes below
 // and 1 above in x and y (the top plane is reused as the next layer's bottom).
+// Planes are staged with cp.async (zero-filled outside the interior) into a
+// ring of 2p+1 slots, so the next layer's planes load while this one computes.
 //   z: each thread contracts its own column in registers; the top output of a
 //      layer is carried to the next layer's bottom node;
 //   x: item (plane c, row y, element) -> p outputs written to a work buffer;
@@ -29,8 +31,9 @@
 // weights, and stores.  The upper Dirichlet faces (index n-1) are written 0.
 //
 // MODE 0: out = A x.
-// MODE 1: PCG step (Sec. 5.3): p_new = z + beta p_old (p_new = z first), staged
-//         on load; out2 = p_new, out = q = A p_new; p_new . q -> alpha.
+// MODE 1: PCG step (Sec. 5.3) on the staged z: w = A z, then for owned nodes
+//         p = z + beta p, q = w + beta q in place (p = z, q = w first), which is
+//         q = A p by linearity; p . q -> alpha = (r.z)/(p.q).
 // MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A); r.r, r.z, b.b.
 #pragma once
 #include "sg_common.cuh"
@@ -54,8 +57,9 @@ struct SemTile {
   static constexpr int TEX = (P <= 2) ? 8 : (P <= 4 ? 4 : 2);
   static constexpr int TEY = (P <= 2) ? 4 : 2;
   static constexpr int TX = TEX * P, TY = TEY * P;
-  static constexpr int PX = TX + P + 1, PY = TY + P + 1, NPL = P + 1;
+  static constexpr int PX = TX + P + 1, PY = TY + P + 1, NPL = 2 * P + 1;  // ring slots
   static constexpr int NTHREADS = TX * TY;
+  static constexpr int MINB = (NTHREADS <= 256) ? 3 : 1;   // CTAs per SM to fit registers for
   static constexpr int N = P + 1, H = (P + 1) / 2;
   static constexpr bool MID = ((P + 1) % 2) == 1;
   static constexpr int HE = H + (MID ? 1 : 0);   // even-part outputs (incl. middle)
@@ -63,11 +67,11 @@ struct SemTile {
 
 template <typename T>
 struct SemArgs {
-  const T* x;     // MODE 0/2: input x     MODE 1: z
-  const T* aux;   // MODE 1: p_old          MODE 2: b
+  const T* x;     // staged operand: MODE 0/2: x     MODE 1: z
+  const T* aux;   // MODE 2: b
   const T* invd;  // MODE 2: 1/diag(A)
-  T* out;         // MODE 0: y   MODE 1: q      MODE 2: r
-  T* out2;        // MODE 1: p_new            MODE 2: z
+  T* out;         // MODE 0: y   MODE 1: q (in/out)   MODE 2: r
+  T* out2;        // MODE 1: p (in/out)             MODE 2: z
   double* partials;
   PcgState* st;
   int zl;         // element layers per CTA
@@ -155,16 +159,32 @@ __device__ __forceinline__ T dir_row(const T (&u)[P + 1], const EOTab<T, P>& st,
   else return row_dot<T, P>(u, st);
 }
 
+// cp.async of one element, zero-filled when !valid (nothing is read then).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst_smem);
+  const int sz = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(src), "r"(sz) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename T, int P, int MODE>
-__global__ void __launch_bounds__(SemTile<P>::NTHREADS)
+__global__ void __launch_bounds__(SemTile<P>::NTHREADS, SemTile<P>::MINB)
 k_sem(const SemGeom g, const SemArgs<T> a) {
   using TL = SemTile<P>;
   constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL;
   constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
-  constexpr bool CREG = sizeof(T) == 4;   // FP32: coefficients in registers
+  constexpr int PLANE = PX * PY;
+  constexpr int K = (PLANE + NT - 1) / NT;       // staged elements per thread per plane
+  constexpr bool CREG = sizeof(T) == 4;          // FP32: coefficients in registers
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);               // NPL planes of PY x PX
-  T* Wb = S + (size_t)NPL * PY * PX;                   // P planes of TY x TX (x / y results)
+  T* S = reinterpret_cast<T*>(smem_raw);         // NPL ring slots of PY x PX
+  T* Wb = S + (size_t)NPL * PLANE;               // P planes of TY x TX (x / y results)
   __shared__ EOTab<T, P> sTab[4];
   __shared__ T sW[P + 1];
   __shared__ double sred[32 * 3];
@@ -187,38 +207,59 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   __syncthreads();
   if (MODE == 1 && s_skip) return;
 
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int e0 = blockIdx.z * a.zl;
+  const int e1 = min(g.ez, e0 + a.zl);
+  const size_t nxy = (size_t)g.nx * g.ny;
+
+  // per-thread staging offsets of the padded plane (same for every plane)
+  int soff[K];
+  bool sval[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = tid + k * NT;
+    const int py = i / PX, px = i - py * PX;
+    const int gxk = x0 - P + px, gyk = y0 - P + py;
+    sval[k] = (i < PLANE) && gxk > 0 && gyk > 0 && gxk < g.nx - 1 && gyk < g.ny - 1;
+    soff[k] = sval[k] ? gxk + g.nx * gyk : 0;
+  }
+  auto stage_plane = [&](int gz) {
+    T* plane = S + (size_t)(gz % NPL) * PLANE;
+    const bool zok = gz > 0 && gz < g.nz - 1;
+    const T* base = a.x + (zok ? (size_t)gz * nxy : 0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = tid + k * NT;
+      if (i < PLANE) cp_async_elem(plane + i, base + soff[k], zok && sval[k]);
+    }
+  };
+
   EOTab<T, P> rt;                 // FP32: register copy of the unscaled table
   if constexpr (CREG) rt = sTab[3];
   const T sx = (T)g.adir[0], sy = (T)g.adir[1], sz = (T)g.adir[2];
 
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int e0 = blockIdx.z * a.zl;
-  const int e1 = min(g.ez, e0 + a.zl);
   const int gx = x0 + tx, gy = y0 + ty;
   const int ia = tx % P, ib = ty % P;
   const bool col_in = (gx < g.nx - 1) && (gy < g.ny - 1);
   const bool col_int = col_in && gx > 0 && gy > 0;
   const T wxy = sW[ia] * sW[ib];
   const T cm = (T)g.cm;
-  const size_t nxy = (size_t)g.nx * g.ny;
 
-  auto operand = [&](int px, int py, int pz) -> T {
-    if (px <= 0 || py <= 0 || pz <= 0 || px >= g.nx - 1 || py >= g.ny - 1 || pz >= g.nz - 1)
-      return (T)0;
-    size_t idx = (size_t)px + (size_t)g.nx * py + nxy * pz;
-    if (MODE == 1) {
-      T zv = a.x[idx];
-      return s_first ? zv : zv + s_beta * a.aux[idx];
-    }
-    return a.x[idx];
-  };
+  // prologue: stage the first layer (all p+1 planes)
+  if (e0 < e1) {
+    for (int pl = 0; pl <= P; ++pl) stage_plane(e0 * P + pl);
+    cp_async_commit();
+  }
 
   // z-carry from the element layer below the chunk (row p on its line)
   T carry = (T)0;
   if (e0 > 0 && col_int) {
     T ub[P + 1];
 #pragma unroll
-    for (int l = 0; l <= P; ++l) ub[l] = operand(gx, gy, (e0 - 1) * P + l);
+    for (int l = 0; l <= P; ++l) {
+      const int gz = (e0 - 1) * P + l;
+      ub[l] = (gz > 0) ? a.x[(size_t)gx + (size_t)g.nx * gy + nxy * gz] : (T)0;
+    }
     carry = dir_row<T, P, CREG>(ub, sTab[2], rt, sz);
   }
 
@@ -226,19 +267,16 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   const int xi_e = tid % TEX, xi_r = (tid / TEX) % TY, xi_c = tid / (TEX * TY);
   const int yi_e = tid % TEY, yi_r = (tid / TEY) % TX, yi_c = tid / (TEY * TX);
 
-  double acc_red[3] = {0.0, 0.0, 0.0};
+  T red[3] = {(T)0, (T)0, (T)0};
 
   for (int e = e0; e < e1; ++e) {
-    // ---- stage planes e*P .. e*P + P (the bottom plane is kept from the last layer)
-    __syncthreads();
-    const int pl0 = (e == e0) ? 0 : 1;
-    for (int pl = pl0; pl <= P; ++pl) {
-      const int gz = e * P + pl;
-      T* plane = S + (size_t)(gz % NPL) * PY * PX;
-      for (int i = tid; i < PY * PX; i += NT) {
-        int py = i / PX, px = i - py * PX;
-        plane[i] = operand(x0 - P + px, y0 - P + py, gz);
-      }
+    // ---- prefetch the next layer's p new planes, then wait for this layer's
+    if (e + 1 < e1) {
+      for (int pl = 1; pl <= P; ++pl) stage_plane((e + 1) * P + pl);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
 
@@ -246,7 +284,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     T u[P + 1], acc[P];
 #pragma unroll
     for (int l = 0; l <= P; ++l)
-      u[l] = S[(size_t)((e * P + l) % NPL) * PY * PX + (ty + P) * PX + (tx + P)];
+      u[l] = S[(size_t)((e * P + l) % NPL) * PLANE + (ty + P) * PX + (tx + P)];
     {
       T o[P + 1];
       dir_line<T, P, CREG>(u, o, sTab[2], rt, sz);
@@ -258,7 +296,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 
     // ---- x: item (plane c, row, element) -> work buffer
     {
-      const T* row = S + (size_t)((e * P + xi_c) % NPL) * PY * PX + (xi_r + P) * PX + xi_e * P;
+      const T* row = S + (size_t)((e * P + xi_c) % NPL) * PLANE + (xi_r + P) * PX + xi_e * P;
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
@@ -275,7 +313,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 
     // ---- y: item (plane c, column, element) -> work buffer
     {
-      const T* col = S + (size_t)((e * P + yi_c) % NPL) * PY * PX + (size_t)(yi_e * P) * PX + (yi_r + P);
+      const T* col = S + (size_t)((e * P + yi_c) % NPL) * PLANE + (size_t)(yi_e * P) * PX + (yi_r + P);
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
@@ -287,7 +325,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     }
     __syncthreads();
 
-    // ---- combine, weights, store
+    // ---- combine, weights, epilogue
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
@@ -295,23 +333,27 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
       const bool inside = col_int && gz > 0;
       const T yv = inside ? (wxy * sW[c]) * v : (T)0;
       if (col_in) {
-        size_t idx = (size_t)gx + (size_t)g.nx * gy + nxy * gz;
+        const size_t idx = (size_t)gx + (size_t)g.nx * gy + nxy * gz;
         if (MODE == 0) {
           a.out[idx] = yv;
         } else if (MODE == 1) {
-          const T pv = u[c];
-          a.out[idx] = yv;
+          T qv = yv, pv = u[c];
+          if (!s_first) {
+            qv += s_beta * a.out[idx];
+            pv += s_beta * a.out2[idx];
+          }
+          a.out[idx] = qv;
           a.out2[idx] = pv;
-          acc_red[0] += (double)pv * (double)yv;
+          red[0] += pv * qv;
         } else {
           const T bv = inside ? a.aux[idx] : (T)0;
           const T rv = inside ? bv - yv : (T)0;
           const T zv = rv * a.invd[idx];
           a.out[idx] = rv;
           if (!a.final_pass) a.out2[idx] = zv;
-          acc_red[0] += (double)rv * (double)rv;
-          acc_red[1] += (double)rv * (double)zv;
-          acc_red[2] += (double)bv * (double)bv;
+          red[0] += rv * rv;
+          red[1] += rv * zv;
+          red[2] += bv * bv;
         }
       }
     }
@@ -319,6 +361,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 
   // ---- upper Dirichlet faces (index n-1) inside this CTA's region: write 0
   {
+    const int tid2 = tid;
     const bool lastx = (x0 + TX >= g.nx - 1), lasty = (y0 + TY >= g.ny - 1);
     const bool lastz = (e1 == g.ez);
     if (lastx || lasty || lastz) {
@@ -326,7 +369,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
       const int z0 = e0 * P, ze = lastz ? g.nz : e1 * P;
       const int wx = xe - x0, wy = ye - y0, wz = ze - z0;
       const int total = wx * wy * wz;
-      for (int i = tid; i < total; i += NT) {
+      for (int i = tid2; i < total; i += NT) {
         int lx = i % wx, ly = (i / wx) % wy, lz = i / (wx * wy);
         int px = x0 + lx, py = y0 + ly, pz = z0 + lz;
         if (px == g.nx - 1 || py == g.ny - 1 || pz == g.nz - 1) {
@@ -339,7 +382,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   }
 
   if (MODE == 1) {
-    double v[1] = {acc_red[0]}, tot[1];
+    double v[1] = {(double)red[0]}, tot[1];
     if (grid_reduce_last<1>(v, a.partials, &a.st->counter[0], sred, tot)) {
       if (tid == 0) {
         PcgState* st = a.st;
@@ -355,7 +398,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
       }
     }
   } else if (MODE == 2) {
-    double v[3] = {acc_red[0], acc_red[1], acc_red[2]}, tot[3];
+    double v[3] = {(double)red[0], (double)red[1], (double)red[2]}, tot[3];
     if (grid_reduce_last<3>(v, a.partials, &a.st->counter[0], sred, tot)) {
       if (tid == 0) {
         PcgState* st = a.st;
