@@ -112,9 +112,10 @@ class Clocks:
 class Workload:
     """Right-hand sides b_k = A x*(t_k) + noise built on the device (untimed)."""
 
-    def __init__(self, sg, torch, nsteps, device):
+    def __init__(self, sg, torch, nsteps, device, cfg=None):
         self.torch = torch
-        c = CFG
+        c = CFG if cfg is None else cfg
+        self.cfg = c
         self.op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
         cx, cy, cz = self.op.coords_1d()
         modes = Modes(c["seed"], c["modes"], c["kmax"])
@@ -136,7 +137,56 @@ class Workload:
                 mask = (b != 0).to(torch.float64)
                 b = b + c["noise"] * rms * eta * mask
             self.rhs.append(b.contiguous())
+        del phi, aphi
         torch.cuda.synchronize()
+
+
+def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
+    """C3-style steps: mode 'ir' = FP32 history + FP32 PCG in FP64 refinement,
+    mode 'f64' = FP64 history + FP64 PCG.  Returns per-step ms and iterations."""
+    c = wl.cfg
+    tol = c["tol"]
+    n = wl.op.n
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    its, outs, rels = [], [], []
+    if mode == "ir":
+        ms = sg.MixedSolver(*c["E"], c["p"], c["lam"])
+        g = sg.Guess(n, s, "extrap", m=m, dtype="f32")
+        x64 = ms.op64.zeros()
+    else:
+        op = wl.op
+        g = sg.Guess(n, s, "extrap", m=m, dtype="f64")
+    for k in range(warmup + steps):
+        timed = k >= warmup
+        if timed and k == warmup:
+            torch.cuda.synchronize()
+            sg.profile_reset()
+            sg.profile_enable(True)
+        if timed:
+            ev[k - warmup][0].record()
+        b = wl.rhs[k]
+        slot = g.next_slot()
+        g.form(None, slot)
+        if mode == "ir":
+            sg.convert(slot, x64)
+            o, i, r = ms.solve(b, x64, tol, inner_tol=1e-5)
+            sg.convert(x64, slot)
+            outs.append(o)
+        else:
+            i, r = op.pcg(b, slot, tol)
+        g.update(slot)
+        if timed:
+            ev[k - warmup][1].record()
+            its.append(i)
+            rels.append(r)
+        flush()
+    torch.cuda.synchronize()
+    sg.profile_enable(False)
+    ex_ms, ex_cnt = sg.profile_read(sg.PROF_EXTRAP)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    return {"ms": sum(ms_steps) / len(ms_steps), "iters": sum(its) / len(its), "max_relres": max(rels),
+            "outer": (sum(outs) / len(outs)) if outs else None,
+            "extrap_avg_ms": ex_ms / max(ex_cnt, 1)}
 
 
 def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, clocks=None, e2e=False):
@@ -269,6 +319,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the ZERO/LAST/QR comparison runs")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32+IR vs FP64 comparison")
+    ap.add_argument("--mixed-steps", type=int, default=8)
+    ap.add_argument("--mixed-warmup", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
@@ -382,6 +435,27 @@ def main():
                           "cg_iters_per_step": sum(r["iters"]) / len(r["iters"])}
         comp["extrap(2,8)"] = {"ms_per_step": ms_step, "cg_iters_per_step": out["cg_iters_per_step"]}
         out["methods"] = comp
+
+    if not args.no_mixed:
+        c3 = CONFIGS["c3"]
+        del wl
+        torch.cuda.empty_cache()
+        w3 = Workload(sg, torch, args.mixed_warmup + args.mixed_steps, device, cfg=c3)
+        r_ir = run_mixed(sg, torch, w3, c3["s"], 2, args.mixed_steps, args.mixed_warmup, flush, "ir")
+        r_64 = run_mixed(sg, torch, w3, c3["s"], 2, args.mixed_steps, args.mixed_warmup, flush, "f64")
+        n3 = w3.op.n
+        ex32_gbs = (c3["s"] + 1) * 4 * n3 / (r_ir["extrap_avg_ms"] * 1e-3) / 1e9
+        out["mixed_precision"] = {
+            "workload": "poisson-32x32x32-p7 (%d nodes), EXTRAP(2,8), tol 1e-10 on the FP64 residual" % n3,
+            "steps": args.mixed_steps, "warmup": args.mixed_warmup,
+            "fp32_ir": {"ms_per_step": r_ir["ms"], "inner_fp32_iters_per_step": r_ir["iters"],
+                        "outer_steps_per_step": r_ir["outer"], "max_relres_fp64": r_ir["max_relres"]},
+            "fp64": {"ms_per_step": r_64["ms"], "cg_iters_per_step": r_64["iters"],
+                     "max_relres": r_64["max_relres"]},
+            "speedup_fp32_ir_vs_fp64": r_64["ms"] / r_ir["ms"],
+            "extrap_fp32": {"GB_s": ex32_gbs, "frac_of_hbm": ex32_gbs / hbm_gbs,
+                            "bytes_per_launch": (c3["s"] + 1) * 4 * n3}}
+        del w3
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, its, _, ns = oracle_sample(out["cg_iters_per_step"], samples=3)

@@ -116,6 +116,33 @@ int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int 
                  void* workspace, int* iters, double* relres, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Mixed precision: FP32 operator, PCG vectors and history wrapped in FP64
+ * iterative refinement (the FP32 form of the operator of Sec. 5.1 and of the
+ * PCG of Sec. 5.3, with the FP64 residual deciding convergence).
+ * ------------------------------------------------------------------------ */
+
+/* Element-wise conversion between FP64 and FP32 device vectors of n entries
+ * (dst = (dst type) src).  src_dtype != dst_dtype. */
+int sg_convert(const void* src, int src_dtype, void* dst, int dst_dtype, int64_t n, void* stream);
+
+/* Workspace bytes for sg_ir_solve with this operator pair. */
+size_t sg_ir_workspace_bytes(sg_op_t op64, sg_op_t op32);
+
+/* Solve A x = b to ||b - A x|| <= tol ||b|| (FP64 residual).  op64 (SG_F64)
+ * and op32 (SG_F32) must describe the same mesh, degree and lambda.  b, x:
+ * FP64 device vectors (x: initial guess in, solution out; Dirichlet entries
+ * set to 0).  Each outer step forms r = b - A x in FP64, solves A d = r with
+ * FP32 Jacobi-PCG to ||r_inner|| <= inner_tol ||r|| (at most maxit_inner
+ * iterations, from d = 0) and adds x += d in FP64, until the FP64 residual
+ * meets tol or max_outer steps were taken.  outer_iters, inner_iters (total
+ * FP32 PCG iterations), relres: HOST outputs, may be NULL.  Synchronises
+ * with ``stream`` once per outer step.  Returns SG_OK, SG_NOT_CONVERGED
+ * (max_outer reached) or a negative error. */
+int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double inner_tol,
+                int max_outer, int maxit_inner, void* workspace, int* outer_iters, int* inner_iters,
+                double* relres, void* stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free PCG.  The paper has no counterpart: this entry point is for
  * callers that cannot allocate device memory -- code whose device memory is
  * owned by a host framework that hands out no more, or a time-critical loop

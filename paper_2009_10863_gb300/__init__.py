@@ -52,6 +52,10 @@ SIGNATURES = [
     ("sg_profile_read", _I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     ("sg_profile_reset", _I, []),
     ("sg_launch_count", ctypes.c_longlong, []),
+    ("sg_convert", _I, [_VP, _I, _VP, _I, _I64, _VP]),
+    ("sg_ir_workspace_bytes", _SZ, [_VP, _VP]),
+    ("sg_ir_solve", _I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                         ctypes.POINTER(_D), _VP]),
     ("sg_pcg_solve_noalloc", _I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
 ]
 
@@ -251,6 +255,37 @@ class Guess:
         if self.method in (PROJ_QR, PROJ_CLASSIC):
             return d.value, arr.reshape(self.s, self.s)
         return d.value, arr[:self.s]
+
+
+def convert(src, dst):
+    """dst = src converted between float64 and float32 (device tensors, same size)."""
+    if src.numel() != dst.numel():
+        raise ValueError("size mismatch")
+    _check(lib().sg_convert(_ptr(src), _dtype_code(src.dtype), _ptr(dst), _dtype_code(dst.dtype),
+                            src.numel(), _stream()))
+    return dst
+
+
+class MixedSolver:
+    """FP32 operator + FP32 Jacobi-PCG inside FP64 iterative refinement."""
+
+    def __init__(self, ex, ey, ez, p, lam=0.0):
+        torch = _torch()
+        self.op64 = Op(ex, ey, ez, p, lam, "f64")
+        self.op32 = Op(ex, ey, ez, p, lam, "f32")
+        self.n = self.op64.n
+        nb = int(lib().sg_ir_workspace_bytes(self.op64.h, self.op32.h))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+    def solve(self, b, x, tol, inner_tol=1e-5, max_outer=30, maxit_inner=10000):
+        """Solve in place; returns (outer steps, total inner FP32 iterations, FP64 relres)."""
+        self.op64._vec(b, "b")
+        self.op64._vec(x, "x")
+        oi, ii, rr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().sg_ir_solve(self.op64.h, self.op32.h, _ptr(b), _ptr(x), float(tol), float(inner_tol),
+                                 int(max_outer), int(maxit_inner), _ptr(self.ws), ctypes.byref(oi),
+                                 ctypes.byref(ii), ctypes.byref(rr), _stream()), (OK, NOT_CONVERGED))
+        return oi.value, ii.value, rr.value
 
 
 def profile_enable(on=True):

@@ -11,6 +11,7 @@
 // then reads the done flag once; kernels after convergence return at once.
 // Vector traffic: 13 n words per iteration (5 in the operator kernel, 8 in
 // the update).
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -366,4 +367,133 @@ extern "C" int sg_pcg_solve_noalloc(sg_op_t op, const void* b, void* x, double t
                                  criterion, ws, L, iters, relres, s);
   return pcg_run<float, true>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit,
                               criterion, ws, L, iters, relres, s);
+}
+
+// ---------------------------------------------------------------- mixed precision
+// FP32 operator/PCG inside FP64 iterative refinement.  Outer loop (FP64):
+// r = b - A64 x (the true-residual pass of the FP64 operator); stop when
+// ||r|| <= tol ||b||; inner FP32 Jacobi-PCG solves A32 d = r to inner_tol
+// (relative), x += d in FP64.  FP64 arithmetic on the GPU is confined to the
+// outer residual, its norms and the correction.
+
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+__global__ void k_add_correction(double* __restrict__ x, const float* __restrict__ d, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+namespace {
+struct IrLayout { size_t state, partials, r64, r32, d32, ws32, total; PcgLayout L32; };
+
+IrLayout ir_layout(sg_op_t op64, sg_op_t op32) {
+  IrLayout I{};
+  const size_t n = (size_t)op64->n;
+  const PcgLayout L64 = layout_for(op64);
+  I.L32 = layout_for(op32);
+  size_t off = 0;
+  I.state = off; off += align_up(sizeof(PcgState));
+  I.partials = off; off += align_up(sizeof(double) * 4 * (size_t)L64.max_blocks);
+  I.r64 = off; off += align_up(8 * n);
+  I.r32 = off; off += align_up(4 * n);
+  I.d32 = off; off += align_up(4 * n);
+  I.ws32 = off; off += I.L32.total;
+  I.total = off;
+  return I;
+}
+
+int flat_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256, cap = 16LL * sg_num_sms();
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+bool same_geometry(sg_op_t a, sg_op_t b) {
+  return a->n == b->n && a->g.p == b->g.p && a->g.ex == b->g.ex && a->g.ey == b->g.ey &&
+         a->g.ez == b->g.ez && a->lambda == b->lambda;
+}
+}  // namespace
+
+extern "C" int sg_convert(const void* src, int src_dtype, void* dst, int dst_dtype, int64_t n, void* stream) {
+  if (!src || !dst || n < 0 || n >= (1LL << 31)) return sg_fail(SG_ERR_INVALID, "convert: bad argument");
+  cudaStream_t s = as_stream(stream);
+  const int nb = flat_blocks(n);
+  if (src_dtype == SG_F64 && dst_dtype == SG_F32)
+    k_convert<double, float><<<nb, 256, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), (int)n);
+  else if (src_dtype == SG_F32 && dst_dtype == SG_F64)
+    k_convert<float, double><<<nb, 256, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), (int)n);
+  else
+    return sg_fail(SG_ERR_INVALID, "convert: only F64 <-> F32");
+  SG_LAUNCH_CHECK("k_convert");
+  return SG_OK;
+}
+
+extern "C" size_t sg_ir_workspace_bytes(sg_op_t op64, sg_op_t op32) {
+  if (!op64 || !op32) return 0;
+  return ir_layout(op64, op32).total;
+}
+
+extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double inner_tol,
+                           int max_outer, int maxit_inner, void* workspace, int* outer_iters,
+                           int* inner_iters, double* relres, void* stream) {
+  if (!op64 || !op32 || !b || !x || !workspace) return sg_fail(SG_ERR_INVALID, "ir_solve: NULL argument");
+  if (op64->dtype != SG_F64 || op32->dtype != SG_F32)
+    return sg_fail(SG_ERR_INVALID, "ir_solve: needs an FP64 and an FP32 operator");
+  if (!same_geometry(op64, op32)) return sg_fail(SG_ERR_INVALID, "ir_solve: operators differ in mesh or lambda");
+  if (!(tol > 0.0) || !(inner_tol > 0.0)) return sg_fail(SG_ERR_INVALID, "ir_solve: tolerances must be > 0");
+  if (max_outer < 0 || maxit_inner < 0) return sg_fail(SG_ERR_INVALID, "ir_solve: iteration limits must be >= 0");
+  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, "ir_solve: vectors must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "ir_solve: workspace must be 256-byte aligned");
+  const IrLayout I = ir_layout(op64, op32);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  PcgState* st = reinterpret_cast<PcgState*>(ws + I.state);
+  double* partials = reinterpret_cast<double*>(ws + I.partials);
+  double* r64 = reinterpret_cast<double*>(ws + I.r64);
+  float* r32 = reinterpret_cast<float*>(ws + I.r32);
+  float* d32 = reinterpret_cast<float*>(ws + I.d32);
+  const double* b64 = static_cast<const double*>(b);
+  double* x64 = static_cast<double*>(x);
+  const int n = (int)op64->n;
+  const int nb = flat_blocks(n);
+  cudaStream_t s = as_stream(stream);
+  k_mask_faces<double><<<64, 256, 0, s>>>(x64, op64->g.nx, op64->g.ny, op64->g.nz);
+  SG_LAUNCH_CHECK("k_mask_faces");
+  int outer = 0, inner_total = 0;
+  double rel = 0.0;
+  PcgState hs;
+  while (true) {
+    k_pcg_setup<<<1, 32, 0, s>>>(st, tol, 0, SG_STOP_REL_B);
+    SG_LAUNCH_CHECK("k_pcg_setup");
+    SemArgs<double> a{};
+    a.x = x64; a.aux = b64; a.out = r64; a.partials = partials; a.st = st; a.final_pass = 1;
+    int rc = sg_sem_launch<double, 2>(op64->g, a, s, 0);
+    if (rc) return rc;
+    SG_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    rel = hs.bb > 0 ? sqrt(hs.rr_true / hs.bb) : sqrt(hs.rr_true);
+    if (!std::isfinite(rel)) return sg_fail(SG_ERR_BREAKDOWN, "ir_solve: non-finite residual");
+    if (rel <= tol || outer >= max_outer) break;
+    k_convert<double, float><<<nb, 256, 0, s>>>(r64, r32, n);
+    SG_LAUNCH_CHECK("k_convert");
+    SG_CUDA_TRY(cudaMemsetAsync(d32, 0, sizeof(float) * (size_t)n, s));
+    int it = 0;
+    double rin = 0.0;
+    rc = pcg_run<float>(op32, r32, d32, inner_tol, maxit_inner, SG_STOP_REL_B, ws + I.ws32, I.L32, &it, &rin, s);
+    if (rc < 0) return rc;
+    inner_total += it;
+    k_add_correction<<<nb, 256, 0, s>>>(x64, d32, n);
+    SG_LAUNCH_CHECK("k_add_correction");
+    ++outer;
+  }
+  if (outer_iters) *outer_iters = outer;
+  if (inner_iters) *inner_iters = inner_total;
+  if (relres) *relres = rel;
+  if (rel > tol) {
+    sg_set_error("ir_solve: maximum outer iteration count reached");
+    return SG_NOT_CONVERGED;
+  }
+  return SG_OK;
 }

@@ -34,7 +34,8 @@
 // MODE 1: PCG step (Sec. 5.3) on the staged z: w = A z, then for owned nodes
 //         p = z + beta p, q = w + beta q in place (p = z, q = w first), which is
 //         q = A p by linearity; p . q -> alpha = (r.z)/(p.q).
-// MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A); r.r, r.z, b.b.
+// MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A); r.r, r.z, b.b
+//         (final_pass: r, r.r and b.b only -- the true residual).
 #pragma once
 #include "sg_common.cuh"
 
@@ -348,11 +349,13 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
         } else {
           const T bv = inside ? a.aux[idx] : (T)0;
           const T rv = inside ? bv - yv : (T)0;
-          const T zv = rv * a.invd[idx];
           a.out[idx] = rv;
-          if (!a.final_pass) a.out2[idx] = zv;
+          if (!a.final_pass) {
+            const T zv = rv * a.invd[idx];
+            a.out2[idx] = zv;
+            red[1] += rv * zv;
+          }
           red[0] += rv * rv;
-          red[1] += rv * zv;
           red[2] += bv * bv;
         }
       }
@@ -404,6 +407,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
         PcgState* st = a.st;
         if (a.final_pass) {
           st->rr_true = tot[0];
+          st->bb = tot[2];
         } else {
           st->rr = tot[0];
           st->rz = tot[1];

@@ -362,3 +362,32 @@ def test_c1_sequence_end_to_end(sg, method, mcode):
     # the better guesses must cut iterations versus the zero guess
     if method in ("extrap", "qr"):
         assert sum(t[0] for t in gres[8:]) < sum(rec["iters"] for rec in run_sequence(ref, rhs, 0, 4, tol=c["tol"])[8:])
+
+
+# ---------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("E,p,lam", [((4, 4, 4), 3, 0.0), ((3, 4, 5), 5, 50.0), ((4, 4, 3), 7, 0.0)])
+def test_fp32_ir_reaches_fp64_tolerance(sg, E, p, lam):
+    """FP32 operator/PCG wrapped in FP64 refinement meets ||b - A x|| <= 1e-10 ||b||
+    measured with the FP64 oracle operator; error vs the FP64 oracle solution is
+    reported and bounded."""
+    ref, rng, xs = _problem(E, p, lam, seed=8)
+    b = ref.apply(xs)
+    ms = sg.MixedSolver(*E, p, lam)
+    x = ms.op64.zeros()
+    outer, inner, relg = ms.solve(dev(b), x, 1e-10, inner_tol=1e-5)
+    xg = host(x)
+    rel_oracle = np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b)
+    assert relg <= 1e-10 and rel_oracle <= 1.01e-10
+    assert outer >= 2 and inner > 0
+    xo, _, _, _ = opcg(ref.apply, ref.diagonal(), b, np.zeros(ref.n), 1e-13, interior=ref.interior)
+    assert rel(xg, xo) <= 1e-7
+
+
+def test_convert_roundtrip(sg):
+    x = dev(random_vectors(5, 1, 1001)[0])
+    y = torch.empty(1001, dtype=torch.float32, device="cuda")
+    sg.convert(x, y)
+    z = torch.empty_like(x)
+    sg.convert(y, z)
+    assert np.array_equal(host(y), np.float32(host(x)).astype(np.float64))
+    assert np.array_equal(host(z), host(y))
