@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic import CONFIGS, Modes, noise  # noqa: E402
+from synthetic import BATCHED, BATCHED_COMMON, CONFIGS, Modes, noise  # noqa: E402
 
 METRIC = "ms per time-step solve at 1e-10 rel. residual + CG iters; guess-kernel HBM GB/s"
 CFG = CONFIGS["c2"]
@@ -183,10 +183,87 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
     torch.cuda.synchronize()
     sg.profile_enable(False)
     ex_ms, ex_cnt = sg.profile_read(sg.PROF_EXTRAP)
+    kern = {}
+    for name, kid in (("pcg_apply", sg.PROF_PCG_APPLY), ("pcg_update", sg.PROF_PCG_UPDATE)):
+        t, cnt = sg.profile_read(kid)
+        kern[name] = {"avg_us": 1e3 * t / max(cnt, 1), "launches_per_step": cnt / steps,
+                      "ms_per_step": t / steps}
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     return {"ms": sum(ms_steps) / len(ms_steps), "iters": sum(its) / len(its), "max_relres": max(rels),
             "outer": (sum(outs) / len(outs)) if outs else None,
-            "extrap_avg_ms": ex_ms / max(ex_cnt, 1)}
+            "extrap_avg_ms": ex_ms / max(ex_cnt, 1), "kernels": kern}
+
+
+def run_batched(sg, torch, device, steps, warmup, flush, mode, tune=True):
+    """Four sequences (24^3 Poisson with QR(8); 20^3, 16^3, 12^3 Helmholtz with
+    EXTRAP(3,8)), FP32 histories, FP32 PCG inside FP64 refinement.  mode
+    'batched': one persistent launch per CG iteration for all four systems;
+    'sequential': one mixed-precision solve per system after another."""
+    cfgs = [dict(c, **BATCHED_COMMON) for c in BATCHED]
+    wls = [Workload(sg, torch, warmup + steps, device, cfg=c) for c in cfgs]
+    tol = BATCHED_COMMON["tol"]
+    s = BATCHED_COMMON["s"]
+    guesses, x64s, x32s, b32s = [], [], [], []
+    for c, wl in zip(cfgs, wls):
+        op32 = sg.Op(*c["E"], c["p"], c["lam"], "f32")
+        g = sg.Guess(wl.op.n, s, c["method"], m=c["m"], eps_rel=1e-5, op=op32, dtype="f32")
+        guesses.append((g, op32))
+        x64s.append(torch.zeros(wl.op.n, dtype=torch.float64, device=device))
+        x32s.append(torch.zeros(wl.op.n, dtype=torch.float32, device=device))
+        b32s.append(torch.zeros(wl.op.n, dtype=torch.float32, device=device))
+    tuned = None
+    if mode == "batched":
+        solver = sg.BatchSolver([(c["E"][0], c["E"][1], c["E"][2], c["lam"]) for c in cfgs])
+        if tune:
+            tuned = solver.tune()
+    else:
+        solvers = [sg.MixedSolver(*c["E"], c["p"], c["lam"]) for c in cfgs]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    inner_tot = [0] * len(cfgs)
+    outer_tot = [0] * len(cfgs)
+    launches = 0
+    for k in range(warmup + steps):
+        timed = k >= warmup
+        if timed and k == warmup:
+            torch.cuda.synchronize()
+            launches = sg.launch_count()
+        if timed:
+            ev[k - warmup][0].record()
+        bs = [wl.rhs[k] for wl in wls]
+        for i, (g, op32) in enumerate(guesses):
+            slot = g.next_slot()
+            x0 = slot if slot is not None else x32s[i]
+            if slot is None:
+                sg.convert(bs[i], b32s[i])
+            g.form(b32s[i] if slot is None else None, x0)
+            sg.convert(x0, x64s[i])
+        if mode == "batched":
+            outer, inner, rel = solver.solve(bs, x64s, tol, inner_tol=1e-5)
+        else:
+            outer, inner, rel = [], [], []
+            for i, ms in enumerate(solvers):
+                o, ii, r = ms.solve(bs[i], x64s[i], tol, inner_tol=1e-5)
+                outer.append(o); inner.append(ii); rel.append(r)
+        for i, (g, op32) in enumerate(guesses):
+            slot = g.next_slot()
+            dst = slot if slot is not None else x32s[i]
+            sg.convert(x64s[i], dst)
+            g.update(dst)
+        if timed:
+            ev[k - warmup][1].record()
+            for i in range(len(cfgs)):
+                inner_tot[i] += inner[i]
+                outer_tot[i] += outer[i]
+            assert max(rel) <= tol * 1.0001
+        flush()
+    torch.cuda.synchronize()
+    launches = sg.launch_count() - launches
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"ms_per_step": sum(ms) / len(ms),
+            "inner_fp32_iters_per_step": [t / steps for t in inner_tot],
+            "outer_steps_per_step": [t / steps for t in outer_tot],
+            "library_launches_per_step": launches / steps,
+            "tuned": {"zl": tuned[0], "ctas_per_sm": tuned[1], "ms_per_iter": tuned[2]} if tuned else None}
 
 
 def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, clocks=None, e2e=False):
@@ -322,6 +399,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32+IR vs FP64 comparison")
     ap.add_argument("--mixed-steps", type=int, default=8)
     ap.add_argument("--mixed-warmup", type=int, default=10)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-sequences comparison")
+    ap.add_argument("--batched-steps", type=int, default=8)
+    ap.add_argument("--batched-warmup", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
@@ -449,13 +529,25 @@ def main():
             "workload": "poisson-32x32x32-p7 (%d nodes), EXTRAP(2,8), tol 1e-10 on the FP64 residual" % n3,
             "steps": args.mixed_steps, "warmup": args.mixed_warmup,
             "fp32_ir": {"ms_per_step": r_ir["ms"], "inner_fp32_iters_per_step": r_ir["iters"],
-                        "outer_steps_per_step": r_ir["outer"], "max_relres_fp64": r_ir["max_relres"]},
+                        "outer_steps_per_step": r_ir["outer"], "max_relres_fp64": r_ir["max_relres"],
+                        "kernels": r_ir["kernels"]},
             "fp64": {"ms_per_step": r_64["ms"], "cg_iters_per_step": r_64["iters"],
-                     "max_relres": r_64["max_relres"]},
+                     "max_relres": r_64["max_relres"], "kernels": r_64["kernels"]},
             "speedup_fp32_ir_vs_fp64": r_64["ms"] / r_ir["ms"],
             "extrap_fp32": {"GB_s": ex32_gbs, "frac_of_hbm": ex32_gbs / hbm_gbs,
                             "bytes_per_launch": (c3["s"] + 1) * 4 * n3}}
         del w3
+
+    if not args.no_batched:
+        torch.cuda.empty_cache()
+        rb = run_batched(sg, torch, device, args.batched_steps, args.batched_warmup, flush, "batched")
+        rs = run_batched(sg, torch, device, args.batched_steps, args.batched_warmup, flush, "sequential")
+        out["batched"] = {
+            "workload": "4 sequences, p=7: 24^3 Poisson QR(8), 20^3/16^3/12^3 Helmholtz lam=1e3 EXTRAP(3,8); "
+                        "FP32 history + FP32 PCG in FP64 refinement to 1e-10",
+            "steps": args.batched_steps, "warmup": args.batched_warmup,
+            "batched_persistent": rb, "sequential_solves": rs,
+            "speedup_batched_vs_sequential": rs["ms_per_step"] / rb["ms_per_step"]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, its, _, ns = oracle_sample(out["cg_iters_per_step"], samples=3)

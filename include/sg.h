@@ -39,6 +39,7 @@ extern "C" {
 
 typedef struct sg_op_s* sg_op_t;
 typedef struct sg_guess_s* sg_guess_t;
+typedef struct sg_batch_s* sg_batch_t;
 
 enum sg_dtype { SG_F64 = 0, SG_F32 = 1 };
 
@@ -65,11 +66,13 @@ enum sg_status {
   SG_ERR_INVALID = -1,    /* bad argument (size, alignment, dtype, range)    */
   SG_ERR_CUDA = -2,       /* a CUDA runtime call failed                      */
   SG_ERR_BREAKDOWN = -3,  /* PCG: p^T A p <= 0 or a non-finite value         */
+  SG_ERR_TIMEOUT = -4,    /* a bounded device-side wait expired              */
   SG_ERR_STATE = -5       /* call not valid for this handle/method           */
 };
 
 #define SG_MAX_HISTORY 16 /* largest history size s                         */
 #define SG_MAX_DEGREE 8   /* largest GLL degree p                           */
+#define SG_BATCH_MAX 4    /* largest number of systems in one batch         */
 
 int sg_version(void);
 const char* sg_last_error(void);
@@ -141,6 +144,39 @@ size_t sg_ir_workspace_bytes(sg_op_t op64, sg_op_t op32);
 int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double inner_tol,
                 int max_outer, int maxit_inner, void* workspace, int* outer_iters, int* inner_iters,
                 double* relres, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched sequences.  The paper keeps one history space per velocity
+ * component and one for the pressure (Sec. 6.1) and solves each system by
+ * PCG (Sec. 5.3).  A batch advances up to SG_BATCH_MAX such systems -- each on
+ * its own mesh, same degree p = 7, own lambda -- in one persistent cooperative
+ * launch per CG iteration (operator work items of every system, a grid
+ * barrier, vector updates of every system, a second barrier), replayed from a
+ * CUDA graph, inside FP64 iterative refinement.  Histories/guesses stay per
+ * system (sg_guess_* handles).
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes for a batch of nseq systems (ops64[k]: SG_F64, ops32[k]:
+ * SG_F32 operator of the same mesh and lambda, p = 7). */
+size_t sg_batch_workspace_bytes(int nseq, const sg_op_t* ops64, const sg_op_t* ops32);
+/* Create a batch on caller-owned workspace (zeroed here; synchronises). */
+int sg_batch_create(sg_batch_t* b, int nseq, const sg_op_t* ops64, const sg_op_t* ops32, void* workspace);
+int sg_batch_destroy(sg_batch_t b);
+/* Autotuner: times candidate launch shapes (work-item depth in element layers
+ * x CTAs per SM) on the batch and keeps the fastest.  Outputs (HOST, may be
+ * NULL): the chosen depth, CTAs per SM and ms per persistent iteration.
+ * Overwrites the batch's internal vectors; synchronises. */
+int sg_batch_tune(sg_batch_t b, int* best_zl, int* best_blocks_per_sm, double* best_ms, void* stream);
+/* Solve A_k x_k = b_k for every system k to ||b_k - A_k x_k|| <= tol ||b_k||
+ * (FP64 residuals).  bvec[k], xvec[k]: FP64 device vectors (x: initial guess
+ * in, solution out).  Per outer step: FP64 residual of every unconverged
+ * system, one batched FP32 PCG solve to inner_tol (relative), x += d.
+ * outer_iters, inner_iters, relres: HOST arrays of nseq (may be NULL).
+ * Synchronises.  Returns SG_OK, SG_NOT_CONVERGED, SG_ERR_TIMEOUT (a grid
+ * barrier wait expired) or another negative error. */
+int sg_batch_ir_solve(sg_batch_t b, const void* const* bvec, void* const* xvec, double tol, double inner_tol,
+                      int max_outer, int maxit_inner, int* outer_iters, int* inner_iters, double* relres,
+                      void* stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free PCG.  The paper has no counterpart: this entry point is for

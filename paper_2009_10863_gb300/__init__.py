@@ -20,7 +20,8 @@ F64, F32 = 0, 1
 ZERO, LAST, EXTRAP, PROJ_QR, PROJ_CLASSIC, SPEXTRAP = 0, 1, 2, 3, 4, 5
 STOP_REL_B, STOP_INITRESID, STOP_RHS = 0, 1, 2
 OK, NOT_CONVERGED = 0, 1
-ERR_INVALID, ERR_CUDA, ERR_BREAKDOWN, ERR_STATE = -1, -2, -3, -5
+ERR_INVALID, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5
+BATCH_MAX = 4
 MAX_HISTORY, MAX_DEGREE = 16, 8
 PROF_SEM, PROF_PCG_APPLY, PROF_PCG_UPDATE, PROF_EXTRAP = 0, 1, 2, 3
 PROF_PROJ_DOTS, PROF_PROJ_LINCOMB, PROF_PROJ_UPDATE = 4, 5, 6
@@ -56,6 +57,12 @@ SIGNATURES = [
     ("sg_ir_workspace_bytes", _SZ, [_VP, _VP]),
     ("sg_ir_solve", _I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_D), _VP]),
+    ("sg_batch_workspace_bytes", _SZ, [_I, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    ("sg_batch_create", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("sg_batch_destroy", _I, [_VP]),
+    ("sg_batch_tune", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    ("sg_batch_ir_solve", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _D, _I, _I,
+                               ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     ("sg_pcg_solve_noalloc", _I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
 ]
 
@@ -286,6 +293,52 @@ class MixedSolver:
                                  int(max_outer), int(maxit_inner), _ptr(self.ws), ctypes.byref(oi),
                                  ctypes.byref(ii), ctypes.byref(rr), _stream()), (OK, NOT_CONVERGED))
         return oi.value, ii.value, rr.value
+
+
+class BatchSolver:
+    """Up to BATCH_MAX systems (p = 7, own mesh and lambda each) solved together:
+    one persistent launch per FP32 CG iteration inside FP64 refinement."""
+
+    def __init__(self, meshes):
+        """meshes: list of (ex, ey, ez, lam)."""
+        torch = _torch()
+        self.ops64 = [Op(ex, ey, ez, 7, lam, "f64") for ex, ey, ez, lam in meshes]
+        self.ops32 = [Op(ex, ey, ez, 7, lam, "f32") for ex, ey, ez, lam in meshes]
+        k = len(meshes)
+        self.k = k
+        a64 = (ctypes.c_void_p * k)(*[o.h.value for o in self.ops64])
+        a32 = (ctypes.c_void_p * k)(*[o.h.value for o in self.ops32])
+        nb = int(lib().sg_batch_workspace_bytes(k, a64, a32))
+        if nb == 0:
+            raise ValueError("invalid batch")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        h = ctypes.c_void_p()
+        _check(lib().sg_batch_create(ctypes.byref(h), k, a64, a32, _ptr(self.ws)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.sg_batch_destroy(self.h)
+            self.h = None
+
+    def tune(self):
+        zl, bps, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().sg_batch_tune(self.h, ctypes.byref(zl), ctypes.byref(bps), ctypes.byref(ms), _stream()))
+        return zl.value, bps.value, ms.value
+
+    def solve(self, bs, xs, tol, inner_tol=1e-5, max_outer=30, maxit_inner=10000):
+        """Solve every system in place.  Returns (outer, inner, relres) lists."""
+        k = self.k
+        for o, b, x in zip(self.ops64, bs, xs):
+            o._vec(b, "b")
+            o._vec(x, "x")
+        bp = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * k)(*[x.data_ptr() for x in xs])
+        oi, ii, rr = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)()
+        _check(lib().sg_batch_ir_solve(self.h, bp, xp, float(tol), float(inner_tol), int(max_outer),
+                                       int(maxit_inner), oi, ii, rr, _stream()), (OK, NOT_CONVERGED))
+        return list(oi), list(ii), list(rr)
 
 
 def profile_enable(on=True):

@@ -61,6 +61,10 @@ struct SemTile {
   static constexpr int PX = TX + P + 1, PY = TY + P + 1, NPL = 2 * P + 1;  // ring slots
   static constexpr int NTHREADS = TX * TY;
   static constexpr int MINB = (NTHREADS <= 256) ? 3 : 1;   // CTAs per SM to fit registers for
+  template <typename T> static constexpr int minb() { return MINB; }
+  // separate x and y result buffers (2 barriers per layer instead of 4): FP32 only,
+  // where shared memory is not the occupancy limit
+  template <typename T> static constexpr bool two_w() { return sizeof(T) == 4; }
   static constexpr int N = P + 1, H = (P + 1) / 2;
   static constexpr bool MID = ((P + 1) % 2) == 1;
   static constexpr int HE = H + (MID ? 1 : 0);   // even-part outputs (incl. middle)
@@ -81,7 +85,7 @@ struct SemArgs {
 
 // Even-odd coefficient tables of one direction (scaled by the direction factor).
 template <typename T, int P>
-struct EOTab {
+struct __align__(16) EOTab {
   using TL = SemTile<P>;
   T ce[TL::HE][TL::H];   // (C[a][l] + C[a][p-l]) / 2, a < H (+ middle row)
   T co[TL::H][TL::H];    // (C[a][l] - C[a][p-l]) / 2, a < H
@@ -174,43 +178,36 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// One work item: the CTA's element-aligned xy tile (bxi, byi) over element
+// layers [e0, e1) of one mesh.  Adds this item's reduction terms to red[].
+// Used by k_sem (one item per CTA) and by the persistent batched kernel.
 template <typename T, int P, int MODE>
-__global__ void __launch_bounds__(SemTile<P>::NTHREADS, SemTile<P>::MINB)
-k_sem(const SemGeom g, const SemArgs<T> a) {
+__device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, int bxi, int byi, int e0, int e1,
+                                         const T* beta_s, const int* first_s, T (&red)[3]) {
+  // beta_s, first_s: shared-memory scalars of the PCG step (MODE 1), read at use
   using TL = SemTile<P>;
   constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL;
   constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
   constexpr int PLANE = PX * PY;
   constexpr int K = (PLANE + NT - 1) / NT;       // staged elements per thread per plane
-  constexpr bool CREG = sizeof(T) == 4;          // FP32: coefficients in registers
+  constexpr bool CREG = false;                    // coefficients read from shared memory (broadcast)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);         // NPL ring slots of PY x PX
-  T* Wb = S + (size_t)NPL * PLANE;               // P planes of TY x TX (x / y results)
+  constexpr bool TWO_W = TL::template two_w<T>();
+  T* Wb = S + (size_t)NPL * PLANE;               // P planes of TY x TX (x results)
+  T* Wy = TWO_W ? Wb + (size_t)P * TY * TX : Wb; // y results (same buffer for FP64)
   __shared__ EOTab<T, P> sTab[4];
   __shared__ T sW[P + 1];
-  __shared__ double sred[32 * 3];
-  __shared__ int s_skip;
-  __shared__ T s_beta;
-  __shared__ int s_first;
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  if (tid == 0) {
-    if (MODE == 1) {
-      s_skip = a.st->done;
-      s_beta = (T)a.st->beta;
-      s_first = a.st->first;
-    }
-  }
+  __syncthreads();                               // shared memory of a previous item is free
   if (tid < 3) build_eotab<T, P>(g, tid, 1.0, sTab[tid]);
   if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
   if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
-  if (MODE == 1 && s_skip) return;
 
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int e0 = blockIdx.z * a.zl;
-  const int e1 = min(g.ez, e0 + a.zl);
+  const int x0 = bxi * TX, y0 = byi * TY;
   const size_t nxy = (size_t)g.nx * g.ny;
 
   // per-thread staging offsets of the padded plane (same for every plane)
@@ -245,6 +242,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   const bool col_int = col_in && gx > 0 && gy > 0;
   const T wxy = sW[ia] * sW[ib];
   const T cm = (T)g.cm;
+  const size_t colbase = (size_t)gx + (size_t)g.nx * gy;
 
   // prologue: stage the first layer (all p+1 planes)
   if (e0 < e1) {
@@ -268,8 +266,6 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   const int xi_e = tid % TEX, xi_r = (tid / TEX) % TY, xi_c = tid / (TEX * TY);
   const int yi_e = tid % TEY, yi_r = (tid / TEY) % TX, yi_c = tid / (TEY * TX);
 
-  T red[3] = {(T)0, (T)0, (T)0};
-
   for (int e = e0; e < e1; ++e) {
     // ---- prefetch the next layer's p new planes, then wait for this layer's
     if (e + 1 < e1) {
@@ -281,11 +277,15 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     }
     __syncthreads();
 
+    // ring slot of plane e*P + l is slot0 + l (mod NPL)
+    const int slot0 = (e * P) % NPL;
+    auto slot_of = [&](int l) { int sl = slot0 + l; return sl >= NPL ? sl - NPL : sl; };
+
     // ---- z: own column in registers
     T u[P + 1], acc[P];
 #pragma unroll
     for (int l = 0; l <= P; ++l)
-      u[l] = S[(size_t)((e * P + l) % NPL) * PLANE + (ty + P) * PX + (tx + P)];
+      u[l] = S[slot_of(l) * PLANE + (ty + P) * PX + (tx + P)];
     {
       T o[P + 1];
       dir_line<T, P, CREG>(u, o, sTab[2], rt, sz);
@@ -297,7 +297,7 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 
     // ---- x: item (plane c, row, element) -> work buffer
     {
-      const T* row = S + (size_t)((e * P + xi_c) % NPL) * PLANE + (xi_r + P) * PX + xi_e * P;
+      const T* row = S + slot_of(xi_c) * PLANE + (xi_r + P) * PX + xi_e * P;
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
@@ -307,51 +307,73 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
 #pragma unroll
       for (int c = 0; c < P; ++c) w[c] = o[c];
     }
-    __syncthreads();
+    if constexpr (!TWO_W) {
+      __syncthreads();
 #pragma unroll
-    for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
-    __syncthreads();
+      for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
+      __syncthreads();
+    }
+
+    // epilogue operands of this layer's owned nodes, loaded before the y
+    // contraction to overlap their latency with it
+    const size_t lidx = colbase + nxy * (size_t)(e * P);
+    constexpr bool PREF = sizeof(T) == 4;        // FP64: registers are too tight
+    T ea[P], eb[P];
+    if (PREF && (MODE == 1 || MODE == 2)) {
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        const size_t idx = lidx + nxy * (size_t)c;
+        const bool ok = col_in && (MODE == 2 ? (col_int && e * P + c > 0) : !*first_s);
+        ea[c] = ok ? (MODE == 1 ? a.out[idx] : a.aux[idx]) : (T)0;
+        eb[c] = (ok && (MODE == 1 || !a.final_pass)) ? (MODE == 1 ? a.out2[idx] : a.invd[idx]) : (T)0;
+      }
+    }
 
     // ---- y: item (plane c, column, element) -> work buffer
     {
-      const T* col = S + (size_t)((e * P + yi_c) % NPL) * PLANE + (size_t)(yi_e * P) * PX + (yi_r + P);
+      const T* col = S + slot_of(yi_c) * PLANE + (yi_e * P) * PX + (yi_r + P);
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
       dir_line<T, P, CREG>(ue, o, sTab[1], rt, sy);
       o[0] += dir_row<T, P, CREG>(ul, sTab[1], rt, sy);
-      T* w = Wb + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
+      T* w = Wy + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
 #pragma unroll
       for (int c = 0; c < P; ++c) w[(size_t)c * TX] = o[c];
     }
     __syncthreads();
+    if constexpr (TWO_W) {
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
+    }
 
     // ---- combine, weights, epilogue
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
-      const T v = acc[c] + Wb[((size_t)c * TY + ty) * TX + tx];
+      const T v = acc[c] + Wy[((size_t)c * TY + ty) * TX + tx];
       const bool inside = col_int && gz > 0;
       const T yv = inside ? (wxy * sW[c]) * v : (T)0;
       if (col_in) {
-        const size_t idx = (size_t)gx + (size_t)g.nx * gy + nxy * gz;
+        const size_t idx = lidx + nxy * (size_t)c;
         if (MODE == 0) {
           a.out[idx] = yv;
         } else if (MODE == 1) {
           T qv = yv, pv = u[c];
-          if (!s_first) {
-            qv += s_beta * a.out[idx];
-            pv += s_beta * a.out2[idx];
+          if (!*first_s) {
+            const T beta = *beta_s;
+            qv += beta * (PREF ? ea[c] : a.out[idx]);
+            pv += beta * (PREF ? eb[c] : a.out2[idx]);
           }
           a.out[idx] = qv;
           a.out2[idx] = pv;
           red[0] += pv * qv;
         } else {
-          const T bv = inside ? a.aux[idx] : (T)0;
+          const T bv = inside ? (PREF ? ea[c] : a.aux[idx]) : (T)0;
           const T rv = inside ? bv - yv : (T)0;
           a.out[idx] = rv;
           if (!a.final_pass) {
-            const T zv = rv * a.invd[idx];
+            const T zv = rv * (PREF ? eb[c] : a.invd[idx]);
             a.out2[idx] = zv;
             red[1] += rv * zv;
           }
@@ -362,27 +384,51 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     }
   }
 
-  // ---- upper Dirichlet faces (index n-1) inside this CTA's region: write 0
+  // ---- upper Dirichlet faces (index n-1) inside this CTA's region: write 0.
+  // The CTA covers x in [x0, xe), y in [y0, ye), z in [z0, ze) where the end is
+  // extended to n when the CTA is the last one along that axis.
   {
-    const int tid2 = tid;
     const bool lastx = (x0 + TX >= g.nx - 1), lasty = (y0 + TY >= g.ny - 1);
     const bool lastz = (e1 == g.ez);
     if (lastx || lasty || lastz) {
-      const int xe = lastx ? g.nx : x0 + TX, ye = lasty ? g.ny : y0 + TY;
+      const int xe = lastx ? g.nx : min(x0 + TX, g.nx), ye = lasty ? g.ny : min(y0 + TY, g.ny);
       const int z0 = e0 * P, ze = lastz ? g.nz : e1 * P;
       const int wx = xe - x0, wy = ye - y0, wz = ze - z0;
-      const int total = wx * wy * wz;
-      for (int i = tid2; i < total; i += NT) {
-        int lx = i % wx, ly = (i / wx) % wy, lz = i / (wx * wy);
-        int px = x0 + lx, py = y0 + ly, pz = z0 + lz;
-        if (px == g.nx - 1 || py == g.ny - 1 || pz == g.nz - 1) {
-          size_t idx = (size_t)px + (size_t)g.nx * py + nxy * pz;
-          a.out[idx] = (T)0;
-          if (MODE == 1 || (MODE == 2 && !a.final_pass)) a.out2[idx] = (T)0;
-        }
-      }
+      auto zero_at = [&](int px, int py, int pz) {
+        const size_t idx = (size_t)px + (size_t)g.nx * py + nxy * pz;
+        a.out[idx] = (T)0;
+        if (MODE == 1 || (MODE == 2 && !a.final_pass)) a.out2[idx] = (T)0;
+      };
+      if (lastx)   // face x = nx-1
+        for (int i = tid; i < wy * wz; i += NT) zero_at(g.nx - 1, y0 + i % wy, z0 + i / wy);
+      if (lasty)   // face y = ny-1
+        for (int i = tid; i < wx * wz; i += NT) zero_at(x0 + i % wx, g.ny - 1, z0 + i / wx);
+      if (lastz)   // face z = nz-1
+        for (int i = tid; i < wx * wy; i += NT) zero_at(x0 + i % wx, y0 + i / wx, g.nz - 1);
     }
   }
+
+}
+
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(SemTile<P>::NTHREADS, SemTile<P>::template minb<T>())
+k_sem(const SemGeom g, const SemArgs<T> a) {
+  __shared__ double sred[32 * 3];
+  __shared__ int s_skip;
+  __shared__ T s_beta;
+  __shared__ int s_first;
+  const int tid = threadIdx.x + SemTile<P>::TX * threadIdx.y;
+  if (tid == 0) {
+    s_skip = (MODE == 1) ? a.st->done : 0;
+    s_beta = (MODE == 1) ? (T)a.st->beta : (T)0;
+    s_first = (MODE == 1) ? a.st->first : 1;
+  }
+  __syncthreads();
+  if (MODE == 1 && s_skip) return;
+  T red[3] = {(T)0, (T)0, (T)0};
+  const int e0 = blockIdx.z * a.zl;
+  const int e1 = min(g.ez, e0 + a.zl);
+  sem_item<T, P, MODE>(g, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red);
 
   if (MODE == 1) {
     double v[1] = {(double)red[0]}, tot[1];

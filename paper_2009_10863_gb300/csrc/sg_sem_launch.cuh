@@ -14,7 +14,8 @@ int sg_sem_launch_p(const SemGeom& g, const SemArgs<T>& a0, cudaStream_t s, int 
   dim3 block(TL::TX, TL::TY, 1);
   dim3 grid((g.ex + TL::TEX - 1) / TL::TEX, (g.ey + TL::TEY - 1) / TL::TEY,
             (g.ez + a.zl - 1) / a.zl);
-  const size_t smem = sizeof(T) * ((size_t)TL::NPL * TL::PY * TL::PX + (size_t)P * TL::TY * TL::TX);
+  const size_t smem = sizeof(T) * ((size_t)TL::NPL * TL::PY * TL::PX +
+                                    (TL::template two_w<T>() ? 2 : 1) * (size_t)P * TL::TY * TL::TX);
   static bool attr_set = false;   // one attribute call per instantiation
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_sem<T, P, MODE>,

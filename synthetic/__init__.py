@@ -28,13 +28,15 @@ CONFIGS = {
                modes=64, kmax=8, s=6, tol=1e-10, noise=0.0, seed=5),
 }
 
-# batched: four independent sequences (3 Helmholtz lam=1e3, 1 Poisson)
+# batched: four independent sequences (3 Helmholtz lam=1e3, 1 Poisson); the
+# Poisson one uses projection QR(8), the Helmholtz ones EXTRAP(3,8)
 BATCHED = [
-    dict(E=(24, 24, 24), p=7, lam=0.0, seed=40),
-    dict(E=(20, 20, 20), p=7, lam=1e3, seed=41),
-    dict(E=(16, 16, 16), p=7, lam=1e3, seed=42),
-    dict(E=(12, 12, 12), p=7, lam=1e3, seed=43),
+    dict(E=(24, 24, 24), p=7, lam=0.0, seed=40, method="qr", m=0),
+    dict(E=(20, 20, 20), p=7, lam=1e3, seed=41, method="extrap", m=3),
+    dict(E=(16, 16, 16), p=7, lam=1e3, seed=42, method="extrap", m=3),
+    dict(E=(12, 12, 12), p=7, lam=1e3, seed=43, method="extrap", m=3),
 ]
+BATCHED_COMMON = dict(steps=100, dt=0.01, modes=8, kmax=4, s=8, tol=1e-10, noise=0.0)
 
 
 class Modes:

@@ -391,3 +391,50 @@ def test_convert_roundtrip(sg):
     sg.convert(y, z)
     assert np.array_equal(host(y), np.float32(host(x)).astype(np.float64))
     assert np.array_equal(host(z), host(y))
+
+
+# ---------------------------------------------------------------- batched sequences
+def test_batched_ir_solves_every_system(sg):
+    """Four systems of different sizes and lambda in one persistent launch per
+    CG iteration: each meets 1e-10 with the FP64 oracle operator, and agrees
+    with the FP64 oracle solution."""
+    meshes = [(2, 2, 2, 0.0), (2, 1, 1, 1e3), (1, 2, 2, 1e3), (1, 1, 1, 1e3)]
+    bs = sg.BatchSolver(meshes)
+    refs, bvs, xvs, xos = [], [], [], []
+    for k, (ex, ey, ez, lam) in enumerate(meshes):
+        ref, rng, xs = _problem((ex, ey, ez), 7, lam, seed=20 + k)
+        b = ref.apply(xs)
+        refs.append((ref, b))
+        bvs.append(dev(b))
+        xvs.append(torch.zeros(ref.n, dtype=torch.float64, device="cuda"))
+        xo, _, _, _ = opcg(ref.apply, ref.diagonal(), b, np.zeros(ref.n), 1e-13, interior=ref.interior)
+        xos.append(xo)
+    outer, inner, relres = bs.solve(bvs, xvs, 1e-10)
+    for k, (ref, b) in enumerate(refs):
+        xg = host(xvs[k])
+        assert relres[k] <= 1e-10 and outer[k] >= 1 and inner[k] > 0
+        assert np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b) <= 1.01e-10
+        assert rel(xg, xos[k]) <= 1e-7
+    # a second solve from the converged solutions: no outer step is needed
+    outer2, inner2, relres2 = bs.solve(bvs, xvs, 1e-10)
+    assert outer2 == [0, 0, 0, 0] and max(relres2) <= 1e-10
+
+
+def test_batched_tuner_then_mixed_convergence(sg):
+    meshes = [(3, 2, 2, 0.0), (2, 2, 2, 1e3)]
+    bs = sg.BatchSolver(meshes)
+    zl, bps, ms = bs.tune()
+    assert zl in (1, 2, 3, 4) and bps >= 1 and ms > 0
+    refs, bvs, xvs = [], [], []
+    for k, (ex, ey, ez, lam) in enumerate(meshes):
+        ref, rng, xs = _problem((ex, ey, ez), 7, lam, seed=30 + k)
+        b = ref.apply(xs)
+        refs.append((ref, b, xs))
+        bvs.append(dev(b))
+        # system 0 starts at its exact solution: it must stay put while 1 iterates
+        xvs.append(dev(xs) if k == 0 else torch.zeros(ref.n, dtype=torch.float64, device="cuda"))
+    outer, inner, relres = bs.solve(bvs, xvs, 1e-10)
+    assert outer[0] == 0 and inner[0] == 0 and outer[1] >= 1
+    for k, (ref, b, xs) in enumerate(refs):
+        xg = host(xvs[k])
+        assert np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b) <= 1.01e-10
