@@ -179,6 +179,33 @@ int sg_batch_ir_solve(sg_batch_t b, const void* const* bvec, void* const* xvec, 
                       void* stream);
 
 /* ------------------------------------------------------------------------
+ * Time-stepped Helmholtz sequence and its reverse-time adjoint (FP64).
+ * Sequence (implicit time stepping, Sec. 5.2, with the Helmholtz systems of
+ * Eq. VelocityEqn): A x_k = M (lam x_{k-1} + f_k), A = K + lam M (the
+ * operator of sg_op_create with that lambda), M the GLL mass matrix of
+ * Sec. 5.1.  Loss L = sum_k ||x_k - x*_k||^2.  Adjoint, backward in time:
+ * A g_k = 2 (x_k - x*_k) + lam M g_{k+1}; dL/df_k = M g_k;
+ * dL/dlam = sum_k g_k^T M (x_{k-1} - x_k).  All vectors: FP64 device, n
+ * entries; Dirichlet entries of the outputs are 0.  The solves are
+ * sg_pcg_solve calls; these entry points build right-hand sides and
+ * accumulate (deterministically) into a device double *acc.
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes for sg_adjoint_accum / sg_sqdiff_accum (zero it once before
+ * first use; the kernels leave it ready for the next call). */
+size_t sg_seq_workspace_bytes(sg_op_t op);
+/* rhs = M (a x + f); x or f may be NULL (treated as 0), not both. */
+int sg_mass_rhs(sg_op_t op, double a, const void* x, const void* f, void* rhs, void* stream);
+/* rhs = c (x - xs) + a M gnext on interior nodes; gnext may be NULL. */
+int sg_adjoint_rhs(sg_op_t op, double c, const void* x, const void* xs, double a, const void* gnext,
+                   void* rhs, void* stream);
+/* mg = M g (mg may be NULL); acc[0] += g^T M (xprev - x) (xprev NULL = 0). */
+int sg_adjoint_accum(sg_op_t op, const void* g, const void* xprev, const void* x, void* mg, double* acc,
+                     void* workspace, void* stream);
+/* acc[0] += ||x - xs||^2 over interior nodes. */
+int sg_sqdiff_accum(sg_op_t op, const void* x, const void* xs, double* acc, void* workspace, void* stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free PCG.  The paper has no counterpart: this entry point is for
  * callers that cannot allocate device memory -- code whose device memory is
  * owned by a host framework that hands out no more, or a time-critical loop

@@ -63,6 +63,11 @@ SIGNATURES = [
     ("sg_batch_tune", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     ("sg_batch_ir_solve", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _D, _I, _I,
                                ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    ("sg_seq_workspace_bytes", _SZ, [_VP]),
+    ("sg_mass_rhs", _I, [_VP, _D, _VP, _VP, _VP, _VP]),
+    ("sg_adjoint_rhs", _I, [_VP, _D, _VP, _VP, _D, _VP, _VP, _VP]),
+    ("sg_adjoint_accum", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("sg_sqdiff_accum", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("sg_pcg_solve_noalloc", _I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
 ]
 
