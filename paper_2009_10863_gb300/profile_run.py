@@ -1,0 +1,60 @@
+"""Small driver that runs every kernel of the library once or a few times on a
+mesh of the bench's shapes, for profiling (ncu) and quick timing.
+
+    python -m paper_2009_10863_gb300.profile_run --elements 16 --dtype f64
+
+It applies the operator `--reps` times (timed with CUDA events), runs a few
+PCG iterations, forms an EXTRAP(2,8) guess and performs QR(8) history updates.
+"""
+import argparse
+
+import numpy as np
+import torch
+
+import paper_2009_10863_gb300 as sg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--elements", type=int, default=16)
+    ap.add_argument("--p", type=int, default=7)
+    ap.add_argument("--lam", type=float, default=1e5)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--pcg-iters", type=int, default=6)
+    ap.add_argument("--s", type=int, default=8)
+    args = ap.parse_args()
+    from paper_2009_10863_gb300 import build
+    build.build()
+    E = args.elements
+    op = sg.Op(E, E, E, args.p, args.lam, args.dtype)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(op.n, dtype=op.dtype, device="cuda", generator=gen)
+    y = op.empty()
+    for _ in range(args.reps):
+        op.apply(x, out=y)
+    b = op.apply(x)
+    xs = op.zeros()
+    it, _ = op.pcg(b, xs, 1e-10, maxit=args.pcg_iters)
+    g = sg.Guess(op.n, args.s, "extrap", m=2, dtype=args.dtype)
+    q = sg.Guess(op.n, args.s, "qr", eps_rel=1e-6, op=op, dtype=args.dtype)
+    for k in range(args.s + 1):
+        v = x * (1.0 + 0.01 * k) + 0.001 * k
+        g.update(v)
+        q.update(v)
+    x0 = op.zeros()
+    g.form(None, x0)
+    q.form(b, x0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        op.apply(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    print("nodes %d dtype %s apply %.1f us, pcg iterations %d, qr d=%d" %
+          (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, q.info()[0]))
+
+
+if __name__ == "__main__":
+    main()
