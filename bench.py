@@ -34,6 +34,9 @@ CFG = CONFIGS["c2"]
 HEADLINE = ("extrap", 2)          # EXTRAP(m=2, s=8)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
+# PCG iteration) from one ncu capture of the current kernel; None once it changes
+PCG_APPLY_TRAFFIC = 33920512 + 0
 
 
 def peaks():
@@ -484,7 +487,10 @@ def main():
 
     out["roofline"] = {"kernel": "pcg_apply (SEM operator + fused p update, FP64)", "bound": "alu",
                        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                       "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PCG_APPLY_TRAFFIC,
+                       "traffic_note": "ncu dram__bytes_read+write per launch (cold reads of z, p, q; "
+                                       "p and q writes retire to L2), profiles/kernels_helmholtz16_p7_fp64.md",
+                       "algorithmic_bytes_per_launch": 5 * 8 * n,
                        "flops_per_launch": flop_apply, "avg_launch_ms": avg_apply_ms, "launches": cnt_apply,
                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
     out["guess_kernels"] = {
