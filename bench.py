@@ -39,6 +39,16 @@ L2_FLUSH_BYTES = 512 << 20
 PCG_APPLY_TRAFFIC = 33920512 + 0
 
 
+def aggregate_max(value, dist, device):
+    """Max of a per-rank value over all ranks (replicas: the slowest rank decides)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -450,11 +460,7 @@ def main():
                       prof=True, clocks=clocks)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
-    ms_step = sum(head["ms"]) / len(head["ms"])
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = aggregate_max(sum(head["ms"]) / len(head["ms"]), dist, device)
 
     # kernel timing from the library's events (same timed region)
     prof = {}
@@ -505,11 +511,7 @@ def main():
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = run_method(sg, torch, wl, HEADLINE[0], HEADLINE[1], s, args.steps, args.warmup, flush, e2e=True)
-    e2e_ms = sum(e2e["ms"]) / len(e2e["ms"])
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = aggregate_max(sum(e2e["ms"]) / len(e2e["ms"]), dist, device)
     out["e2e"] = {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
     # the other guess methods on the same sequence (not part of the headline)

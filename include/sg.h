@@ -178,6 +178,14 @@ int sg_batch_ir_solve(sg_batch_t b, const void* const* bvec, void* const* xvec, 
                       int max_outer, int maxit_inner, int* outer_iters, int* inner_iters, double* relres,
                       void* stream);
 
+/* Self-test of the bounded device-side wait used by the batched kernel (no
+ * counterpart in the paper): one cooperative launch of one CTA per SM passes
+ * a grid barrier twice.  With extra_blocks > 0 the barrier waits for CTAs that
+ * do not exist, so each wait gives up after spin_limit polls (~64 ns each),
+ * records the expiry and returns; the call then returns SG_ERR_TIMEOUT and the
+ * device stays usable.  scratch: >= 16 bytes of device memory.  Synchronises. */
+int sg_selftest_barrier(int extra_blocks, long long spin_limit, void* scratch, void* stream);
+
 /* ------------------------------------------------------------------------
  * Time-stepped Helmholtz sequence and its reverse-time adjoint (FP64).
  * Sequence (implicit time stepping, Sec. 5.2, with the Helmholtz systems of

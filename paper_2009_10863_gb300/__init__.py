@@ -68,6 +68,7 @@ SIGNATURES = [
     ("sg_adjoint_rhs", _I, [_VP, _D, _VP, _VP, _D, _VP, _VP, _VP]),
     ("sg_adjoint_accum", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("sg_sqdiff_accum", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("sg_selftest_barrier", _I, [_I, ctypes.c_longlong, _VP, _VP]),
     ("sg_pcg_solve_noalloc", _I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
 ]
 

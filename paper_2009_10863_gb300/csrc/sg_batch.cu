@@ -54,7 +54,8 @@ struct BatchArgs {
 };
 
 // Grid-wide barrier for a cooperative launch, bounded spin (error flag on expiry).
-__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err, unsigned int nblocks) {
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err, unsigned int nblocks,
+                                             long long spin_limit = kSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     volatile unsigned int* gen = bar + 1;
@@ -67,7 +68,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err, unsign
     } else {
       long long it = 0;
       while (*gen == g0) {
-        if (++it > kSpinLimit) { atomicExch(err, 1); break; }
+        if (++it > spin_limit) { atomicExch(err, 1); break; }
         __nanosleep(64);
       }
     }
@@ -714,5 +715,45 @@ extern "C" int sg_batch_tune(sg_batch_t b, int* best_zl, int* best_blocks_per_sm
   if (best_zl) *best_zl = bz;
   if (best_blocks_per_sm) *best_blocks_per_sm = bb;
   if (best_ms) *best_ms = best;
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------- barrier self-test
+// One cooperative launch that passes through the grid barrier twice.  With
+// extra_blocks > 0 the barrier expects that many CTAs more than are launched,
+// so its bounded wait must expire: the kernel records the expiry in the error
+// word and returns normally, and the host reports SG_ERR_TIMEOUT.
+__global__ void k_barrier_selftest(unsigned int* bar, int* err, unsigned int expect, long long spin_limit, int* passes) {
+  grid_barrier(bar, err, expect, spin_limit);
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(passes, 1);
+  grid_barrier(bar, err, expect, spin_limit);
+}
+
+extern "C" int sg_selftest_barrier(int extra_blocks, long long spin_limit, void* scratch, void* stream) {
+  if (!scratch || extra_blocks < 0 || spin_limit < 1) return sg_fail(SG_ERR_INVALID, "selftest_barrier: bad argument");
+  cudaStream_t s = as_stream(stream);
+  unsigned int* bar = static_cast<unsigned int*>(scratch);
+  int* err = reinterpret_cast<int*>(bar + 2);
+  int* passes = err + 1;
+  SG_CUDA_TRY(cudaMemsetAsync(scratch, 0, 16, s));
+  int blocks = sg_num_sms();
+  unsigned int expect = (unsigned int)(blocks + extra_blocks);
+  void* params[] = {&bar, &err, &expect, &spin_limit, &passes};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_barrier_selftest, params);
+  sg_count_launch();
+  if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("selftest_barrier launch: ") + cudaGetErrorString(e));
+  int h[2] = {0, 0};
+  SG_CUDA_TRY(cudaMemcpyAsync(h, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h[0]) return sg_fail(SG_ERR_TIMEOUT, "selftest_barrier: grid barrier wait expired");
   return SG_OK;
 }

@@ -38,8 +38,8 @@ def main():
     it, _ = op.pcg(b, xs, 1e-10, maxit=args.pcg_iters)
     g = sg.Guess(op.n, args.s, "extrap", m=2, dtype=args.dtype)
     q = sg.Guess(op.n, args.s, "qr", eps_rel=1e-6, op=op, dtype=args.dtype)
-    for k in range(args.s + 1):
-        v = x * (1.0 + 0.01 * k) + 0.001 * k
+    for k in range(args.s + 1):          # independent vectors: the QR history fills to d = s
+        v = x + 0.1 * torch.randn(op.n, dtype=op.dtype, device="cuda", generator=gen)
         g.update(v)
         q.update(v)
     x0 = op.zeros()

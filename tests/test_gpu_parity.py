@@ -438,3 +438,64 @@ def test_batched_tuner_then_mixed_convergence(sg):
     for k, (ref, b, xs) in enumerate(refs):
         xg = host(xvs[k])
         assert np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b) <= 1.01e-10
+
+
+# ---------------------------------------------------------------- failure detection (no GPU fault)
+def test_bounded_grid_barrier_wait_expires_and_context_survives(sg):
+    """The grid barrier of the batched kernel waits a bounded time: when a CTA
+    never arrives the wait expires, the kernel returns and SG_ERR_TIMEOUT is
+    reported; afterwards the device keeps working."""
+    import ctypes
+    scratch = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert sg.lib().sg_selftest_barrier(0, 1 << 20, ctypes.c_void_p(scratch.data_ptr()), st) == sg.OK
+    rc = sg.lib().sg_selftest_barrier(1, 1 << 14, ctypes.c_void_p(scratch.data_ptr()), st)
+    assert rc == sg.ERR_TIMEOUT and b"expired" in sg.lib().sg_last_error()
+    # the context is intact: a regular solve still works
+    ref, rng, xs = _problem((2, 2, 2), 3, 1.0, seed=40)
+    op = sg.Op(2, 2, 2, 3, 1.0, "f64")
+    x = op.zeros()
+    it, r = op.pcg(dev(ref.apply(xs)), x, 1e-10)
+    assert r <= 1e-10 and it > 0
+
+
+def test_nonfinite_input_reports_breakdown(sg):
+    """A NaN in the right-hand side ends PCG with SG_ERR_BREAKDOWN (host-side fault injection)."""
+    ref, rng, xs = _problem((2, 2, 2), 3, 1.0, seed=41)
+    op = sg.Op(2, 2, 2, 3, 1.0, "f64")
+    b = ref.apply(xs)
+    b[np.flatnonzero(ref.interior)[5]] = np.nan
+    with pytest.raises(sg.SGError) as ei:
+        op.pcg(dev(b), op.zeros(), 1e-10)
+    assert ei.value.code == sg.ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("method", ["extrap", "qr"])
+def test_largest_history(sg, method):
+    """s = SG_MAX_HISTORY = 16 (the largest history) against the oracle."""
+    s = 16
+    if method == "extrap":
+        n = 5001
+        g = sg.Guess(n, s, "extrap", m=3)
+        hist = random_vectors(13, s + 2, n)
+        for k in range(s + 2):
+            g.update(dev(hist[k]))
+        x0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        g.form(None, x0)
+        want = oex.extrap_guess(list(hist[2:]), oex.lsq_coeffs(s, 3))
+        assert rel(host(x0), want) <= 1e-12
+    else:
+        ref = SemOperator(3, 3, 3, 3, 5.0)
+        op = sg.Op(3, 3, 3, 3, 5.0, "f64")
+        g = sg.Guess(ref.n, s, "qr", eps_rel=1e-12, op=op)
+        o = ProjectionQR(s, 1e-12, ref.apply)
+        rng = np.random.default_rng(17)
+        for k in range(s + 3):
+            x = rng.standard_normal(ref.n) * ref.interior
+            g.update(dev(x))
+            o.update(x)
+        assert g.info()[0] == o.d == s
+        b = ref.apply(rng.standard_normal(ref.n) * ref.interior)
+        x0 = op.zeros()
+        g.form(dev(b), x0)
+        assert rel(host(x0), o.form(b, np.zeros(ref.n))) <= 1e-12
