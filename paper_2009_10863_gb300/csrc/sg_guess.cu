@@ -74,6 +74,21 @@ __device__ __forceinline__ float vel(const float4& v, int w) {
 }
 template <typename V> __device__ __forceinline__ V vzero() { V v; for (int w = 0; w < (int)(sizeof(V) / sizeof(v.x)); ++w) vel(v, w) = 0; return v; }
 
+// Column counts are compile-time template arguments: GB300's FP64 pipe is narrow
+// enough that predicated-off multiply-adds of a fixed 16-column loop would cost
+// as much as live ones.  The host dispatches the extrapolation kernel on its
+// term count; the projection kernels read d on the device and switch (block-
+// uniformly) to the body instantiated for that d.
+#define SG_COLS_DISPATCH(d, CALL)                                                         \
+  switch (d) {                                                                            \
+    case 0: CALL(0); break;   case 1: CALL(1); break;   case 2: CALL(2); break;           \
+    case 3: CALL(3); break;   case 4: CALL(4); break;   case 5: CALL(5); break;           \
+    case 6: CALL(6); break;   case 7: CALL(7); break;   case 8: CALL(8); break;           \
+    case 9: CALL(9); break;   case 10: CALL(10); break; case 11: CALL(11); break;         \
+    case 12: CALL(12); break; case 13: CALL(13); break; case 14: CALL(14); break;         \
+    case 15: CALL(15); break; case 16: CALL(16); break; default: break;                   \
+  }
+
 // ---------------------------------------------------------------- extrapolation
 template <typename T>
 struct ExtrapArgs {
@@ -82,32 +97,30 @@ struct ExtrapArgs {
   int k;
 };
 
-template <typename T>
+template <typename T, int K>
 __global__ void __launch_bounds__(256) k_extrap(T* out, const ExtrapArgs<T> a, int n) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  T b[SG_SMAX];
+  T b[K];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) b[j] = (T)a.beta[j];
+  for (int j = 0; j < K; ++j) b[j] = (T)a.beta[j];
   const int nv = n / W;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V v[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = reinterpret_cast<const V*>(a.src[j])[i];   // all loads in flight
     V acc = vzero<V>();
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < a.k) {
-        const V v = reinterpret_cast<const V*>(a.src[j])[i];
+    for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int w = 0; w < W; ++w) vel(acc, w) += b[j] * vel(v, w);
-      }
-    }
+      for (int w = 0; w < W; ++w) vel(acc, w) += b[j] * vel(v[j], w);
     reinterpret_cast<V*>(out)[i] = acc;
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     T acc = 0;
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j)
-      if (j < a.k) acc += b[j] * a.src[j][i];
+    for (int j = 0; j < K; ++j) acc += b[j] * a.src[j][i];
     out[i] = acc;
   }
 }
@@ -132,128 +145,168 @@ __device__ __forceinline__ const typename VecT<T>::V* colv(const T* base, size_t
   return reinterpret_cast<const typename VecT<T>::V*>(base + (size_t)j * stride);
 }
 
+#define SG_NZ(D) ((D) > 0 ? (D) : 1)
+
+// v[j] += slot_j . y for j < D (plain dots; the caller applies column scales)
+template <typename T, int D>
+__device__ __forceinline__ void dots_body(const T* base, size_t stride, const T* y, int n, double (&v)[NV]) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  T acc[SG_NZ(D)];
+#pragma unroll
+  for (int j = 0; j < D; ++j) acc[j] = 0;
+  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+    const V yv = reinterpret_cast<const V*>(y)[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const V cv = colv(base, stride, j)[i];
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(yv, w);
+    }
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc[j] += base[(size_t)j * stride + i] * y[i];
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
+}
+
 // form, pass 1: alpha_j = scale_j * (slot_j . b), j < d
 template <typename T>
 __global__ void __launch_bounds__(256) k_proj_dots(const ProjArgs<T> a) {
-  using V = typename VecT<T>::V;
-  constexpr int W = VecT<T>::W;
   __shared__ double sred[32 * NV];
   const int d = a.st->d;
-  T acc[SG_SMAX];
-#pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
-  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const V bv = reinterpret_cast<const V*>(a.v)[i];
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        const V cv = colv(a.B, a.stride, j)[i];
-#pragma unroll
-        for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(bv, w);
-      }
-    }
-  }
-  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j)
-      if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * a.v[i];
-  }
   double v[NV], tot[NV];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
-  v[SG_SMAX] = 0.0;
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+#define SG_CALL(D) dots_body<T, D>(a.B, a.stride, a.v, a.n, v)
+  SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->alpha[j] = a.st->scale[j] * tot[j];
   }
 }
 
+// out = sum_j c_j slot_j, j < D
+template <typename T, int D>
+__device__ __forceinline__ void lincomb_body(const T* base, size_t stride, const T (&c)[SG_SMAX], T* out, int n) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+    V xs[SG_NZ(D)];
+#pragma unroll
+    for (int j = 0; j < D; ++j) xs[j] = colv(base, stride, j)[i];
+    V acc = vzero<V>();
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int w = 0; w < W; ++w) vel(acc, w) += c[j] * vel(xs[j], w);
+    reinterpret_cast<V*>(out)[i] = acc;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += c[j] * base[(size_t)j * stride + i];
+    out[i] = acc;
+  }
+}
+
 // form, pass 2: x0 = sum_j alpha_j scale_j slot_j of X~ (x0 untouched if d = 0)
 template <typename T>
 __global__ void __launch_bounds__(256) k_proj_lincomb(const ProjArgs<T> a) {
-  using V = typename VecT<T>::V;
-  constexpr int W = VecT<T>::W;
   const int d = a.st->d;
   if (d == 0) return;
   T c[SG_SMAX];
 #pragma unroll
   for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->alpha[j] * a.st->scale[j]) : (T)0;
-  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    V acc = vzero<V>();
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        const V xv = colv(a.X, a.stride, j)[i];
-#pragma unroll
-        for (int w = 0; w < W; ++w) vel(acc, w) += c[j] * vel(xv, w);
-      }
-    }
-    reinterpret_cast<V*>(a.out)[i] = acc;
-  }
-  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    T acc = 0;
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j)
-      if (j < d) acc += c[j] * a.X[(size_t)j * a.stride + i];
-    a.out[i] = acc;
-  }
+#define SG_CALL(D) lincomb_body<T, D>(a.X, a.stride, c, a.out, a.n)
+  SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
 }
 
-// One Givens sweep over a column set at vector index i (App. A: the column
-// shared by successive rotations stays in registers).  Writes new columns
-// 0..d-1; returns nothing for X~, accumulates dots with t for B~.
-template <typename T, bool DOTS>
-__device__ __forceinline__ void givens_sweep_vec(T* base, size_t stride, int i, int d,
-                                                 const T* sc0, const T* gc, const T* gs,
-                                                 const T* gcin, const T* gsin,
-                                                 const typename VecT<T>::V& tv, T* acc) {
+// One Givens sweep over a column set (App. A: the column shared by successive
+// rotations stays in registers): D rotations, new columns 0..D-1 written back,
+// dots of the new B~ columns with t accumulated when DOTS.
+template <typename T, int D, bool DOTS>
+__device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t, int n, T sc0, const T* gc,
+                                             const T* gs, const T* gcin, const T* gsin, T (&acc)[SG_NZ(D)]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  V carry = reinterpret_cast<const V*>(base)[i];
+  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+  // rotation coefficients stay in shared memory (block-uniform broadcast reads)
+  const T* cc = gc;
+  const T* ss = gs;
+  const T* ci = gcin;
+  const T* si = gsin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+    V tv;
+    if (DOTS) tv = reinterpret_cast<const V*>(t)[i];
+    V carry = reinterpret_cast<const V*>(base)[i];
 #pragma unroll
-  for (int w = 0; w < W; ++w) vel(carry, w) *= sc0[0];
+    for (int w = 0; w < W; ++w) vel(carry, w) *= sc0;
 #pragma unroll
-  for (int j = 0; j < SG_SMAX - 1; ++j) {
-    if (j < d) {
+    for (int j = 0; j < D; ++j) {
       const V nx = colv(base, stride, j + 1)[i];
       V o;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         const T cw = vel(carry, w), nw = vel(nx, w);
-        vel(o, w) = gc[j] * cw + gsin[j] * nw;
-        vel(carry, w) = -gs[j] * cw + gcin[j] * nw;
+        vel(o, w) = cc[j] * cw + si[j] * nw;
+        vel(carry, w) = -ss[j] * cw + ci[j] * nw;
         if (DOTS) acc[j] += vel(o, w) * vel(tv, w);
       }
       reinterpret_cast<V*>(base + (size_t)j * stride)[i] = o;
     }
   }
-}
-
-template <typename T, bool DOTS>
-__device__ __forceinline__ void givens_sweep_scalar(T* base, size_t stride, int i, int d,
-                                                    T sc0, const T* gc, const T* gs,
-                                                    const T* gcin, const T* gsin, T tt, T* acc) {
-  T carry = sc0 * base[i];
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
+    const T tt = DOTS ? t[i] : (T)0;
+    T carry = sc0 * base[i];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX - 1; ++j) {
-    if (j < d) {
+    for (int j = 0; j < D; ++j) {
       const T nx = base[(size_t)(j + 1) * stride + i];
-      const T o = gc[j] * carry + gsin[j] * nx;
-      carry = -gs[j] * carry + gcin[j] * nx;
+      const T o = cc[j] * carry + si[j] * nx;
+      carry = -ss[j] * carry + ci[j] * nx;
       if (DOTS) acc[j] += o * tt;
       base[(size_t)j * stride + i] = o;
     }
   }
 }
 
+template <typename T, int D>
+__device__ __forceinline__ void givens_body(const ProjArgs<T>& a, const T* s_sc, const T* s_c, const T* s_s,
+                                            const T* s_cin, const T* s_sin, double (&v)[NV]) {
+  T acc[SG_NZ(D)];
+#pragma unroll
+  for (int j = 0; j < D; ++j) acc[j] = 0;
+  givens_sweep<T, D, true>(a.B, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
+  givens_sweep<T, D, false>(a.X, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
+}
+
+template <typename T>
+__device__ __forceinline__ T sq_norm(const T* t, int n) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  T nn = 0;
+  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+    const V tv = reinterpret_cast<const V*>(t)[i];
+#pragma unroll
+    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) nn += t[i] * t[i];
+  return nn;
+}
+
 // update sweep 1: optional Givens downdate (Algorithm 2, d = M) or classic
 // restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
-  using V = typename VecT<T>::V;
-  constexpr int W = VecT<T>::W;
   __shared__ double sred[32 * NV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
   __shared__ T s_cin[SG_SMAX], s_sin[SG_SMAX], s_c[SG_SMAX], s_s[SG_SMAX], s_sc[SG_SMAX];
@@ -297,45 +350,19 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   __syncthreads();
   const int d = s_d;
   const int rot = s_rot;
-  T acc[SG_SMAX];
-#pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
-  T nn = 0;
-  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const V tv = reinterpret_cast<const V*>(a.t)[i];
-#pragma unroll
-    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
-    if (rot) {
-      givens_sweep_vec<T, true>(a.B, a.stride, i, d, s_sc, s_c, s_s, s_cin, s_sin, tv, acc);
-      givens_sweep_vec<T, false>(a.X, a.stride, i, d, s_sc, s_c, s_s, s_cin, s_sin, tv, acc);
-    } else {
-#pragma unroll
-      for (int j = 0; j < SG_SMAX; ++j) {
-        if (j < d) {
-          const V cv = colv(a.B, a.stride, j)[i];
-#pragma unroll
-          for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(tv, w);
-        }
-      }
-    }
-  }
-  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const T tt = a.t[i];
-    nn += tt * tt;
-    if (rot) {
-      givens_sweep_scalar<T, true>(a.B, a.stride, i, d, s_sc[0], s_c, s_s, s_cin, s_sin, tt, acc);
-      givens_sweep_scalar<T, false>(a.X, a.stride, i, d, s_sc[0], s_c, s_s, s_cin, s_sin, tt, acc);
-    } else {
-#pragma unroll
-      for (int j = 0; j < SG_SMAX; ++j)
-        if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
-    }
-  }
   double v[NV], tot[NV];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
-  v[SG_SMAX] = (double)nn;
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  if (rot) {
+#define SG_CALL(D) givens_body<T, D>(a, s_sc, s_c, s_s, s_cin, s_sin, v)
+    SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
+  } else {
+#define SG_CALL(D) dots_body<T, D>(a.B, a.stride, a.t, a.n, v)
+    SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
+  }
+  v[SG_SMAX] = (double)sq_norm<T>(a.t, a.n);
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (tid == 0) {
       ProjState* st = a.st;
@@ -355,66 +382,106 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   }
 }
 
-// update sweep 2: t -= B~ c1; c2 = B~^T t
-template <typename T>
-__global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
+// t -= sum_j c_j slot_j (D columns), then v[j] = slot_j . t
+template <typename T, int D>
+__device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[NV]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  __shared__ double sred[32 * NV];
-  const int d = a.st->d;
-  T c[SG_SMAX];
+  T acc[SG_NZ(D)];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->c1[j] * a.st->scale[j]) : (T)0;
-  T acc[SG_SMAX];
-#pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) acc[j] = 0;
+  for (int j = 0; j < D; ++j) acc[j] = 0;
   const int nv = a.n / W, stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
     V tv = reinterpret_cast<const V*>(a.t)[i];
+    V cols[SG_NZ(D)];
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        const V b = colv(a.B, a.stride, j)[i];
+    for (int j = 0; j < D; ++j) cols[j] = colv(a.B, a.stride, j)[i];
 #pragma unroll
-        for (int w = 0; w < W; ++w) vel(tv, w) -= c[j] * vel(b, w);
-      }
-    }
+    for (int j = 0; j < D; ++j)
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        const V b = colv(a.B, a.stride, j)[i];   // L1 hit
+      for (int w = 0; w < W; ++w) vel(tv, w) -= c[j] * vel(cols[j], w);
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[j] += vel(b, w) * vel(tv, w);
-      }
-    }
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[j] += vel(cols[j], w) * vel(tv, w);
     reinterpret_cast<V*>(a.t)[i] = tv;
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     T tt = a.t[i];
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j)
-      if (j < d) tt -= c[j] * a.B[(size_t)j * a.stride + i];
+    for (int j = 0; j < D; ++j) tt -= c[j] * a.B[(size_t)j * a.stride + i];
 #pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j)
-      if (j < d) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
+    for (int j = 0; j < D; ++j) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
     a.t[i] = tt;
   }
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
+}
+
+// update sweep 2: t -= B~ c1; c2 = B~^T t
+template <typename T>
+__global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
+  __shared__ double sred[32 * NV];
+  const int d = a.st->d;
+  T c[SG_SMAX];
+#pragma unroll
+  for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->c1[j] * a.st->scale[j]) : (T)0;
   double v[NV], tot[NV];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = (double)acc[j];
-  v[SG_SMAX] = 0.0;
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+#define SG_CALL(D) upd2_body<T, D>(a, c, v)
+  SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->c2[j] = a.st->scale[j] * tot[j];
   }
 }
 
+// b~ = t - sum c2_j B_j -> Bd; x~ = x - sum cx_j X_j -> Xd; returns ||b~||^2
+template <typename T, int D>
+__device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SMAX], const T (&cx)[SG_SMAX],
+                                       T* Bd, T* Xd) {
+  using V = typename VecT<T>::V;
+  constexpr int W = VecT<T>::W;
+  T nn = 0;
+  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    V tv = reinterpret_cast<const V*>(a.t)[i];
+    V xv = reinterpret_cast<const V*>(a.v)[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const V bc = colv(a.B, a.stride, j)[i];
+      const V xc = colv(a.X, a.stride, j)[i];
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        vel(tv, w) -= c2[j] * vel(bc, w);
+        vel(xv, w) -= cx[j] * vel(xc, w);
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+    reinterpret_cast<V*>(Bd)[i] = tv;
+    reinterpret_cast<V*>(Xd)[i] = xv;
+  }
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    T tt = a.t[i], xx = a.v[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      tt -= c2[j] * a.B[(size_t)j * a.stride + i];
+      xx -= cx[j] * a.X[(size_t)j * a.stride + i];
+    }
+    nn += tt * tt;
+    Bd[i] = tt;
+    Xd[i] = xx;
+  }
+  return nn;
+}
+
 // update sweep 3: b~ = t - B~ c2 -> B~ slot d; x~ = x_k - X~ (c1 + c2) -> X~ slot d;
 // ||b~||^2; acceptance test and R column (Algorithm 2, last block)
 template <typename T>
 __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
-  using V = typename VecT<T>::V;
-  constexpr int W = VecT<T>::W;
   __shared__ double sred[32 * NV];
   const int d = a.st->d;
   T c2[SG_SMAX], cx[SG_SMAX];
@@ -426,40 +493,9 @@ __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   T* Bd = a.B + (size_t)d * a.stride;
   T* Xd = a.X + (size_t)d * a.stride;
   T nn = 0;
-  const int nv = a.n / W, stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    V tv = reinterpret_cast<const V*>(a.t)[i];
-    V xv = reinterpret_cast<const V*>(a.v)[i];
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        const V bc = colv(a.B, a.stride, j)[i];
-        const V xc = colv(a.X, a.stride, j)[i];
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          vel(tv, w) -= c2[j] * vel(bc, w);
-          vel(xv, w) -= cx[j] * vel(xc, w);
-        }
-      }
-    }
-#pragma unroll
-    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
-    reinterpret_cast<V*>(Bd)[i] = tv;
-    reinterpret_cast<V*>(Xd)[i] = xv;
-  }
-  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    T tt = a.t[i], xx = a.v[i];
-#pragma unroll
-    for (int j = 0; j < SG_SMAX; ++j) {
-      if (j < d) {
-        tt -= c2[j] * a.B[(size_t)j * a.stride + i];
-        xx -= cx[j] * a.X[(size_t)j * a.stride + i];
-      }
-    }
-    nn += tt * tt;
-    Bd[i] = tt;
-    Xd[i] = xx;
-  }
+#define SG_CALL(D) nn = upd3_body<T, D>(a, c2, cx, Bd, Xd)
+  SG_COLS_DISPATCH(d, SG_CALL)
+#undef SG_CALL
   double v[NV], tot[NV];
 #pragma unroll
   for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
@@ -556,7 +592,19 @@ int extrap_form(sg_guess_t g, void* x0, cudaStream_t s) {
   }
   a.k = nt;
   ProfScope ps(PROF_EXTRAP, s);
-  k_extrap<T><<<reduce_blocks(g->n, VecT<T>::W) * 2, 256, 0, s>>>(static_cast<T*>(x0), a, (int)g->n);
+  const int nb = reduce_blocks(g->n, VecT<T>::W) * 2;
+  T* out = static_cast<T*>(x0);
+  const int n = (int)g->n;
+#define SG_CALL(K) k_extrap<T, K><<<nb, 256, 0, s>>>(out, a, n)
+  switch (nt) {
+    case 1: SG_CALL(1); break;   case 2: SG_CALL(2); break;   case 3: SG_CALL(3); break;
+    case 4: SG_CALL(4); break;   case 5: SG_CALL(5); break;   case 6: SG_CALL(6); break;
+    case 7: SG_CALL(7); break;   case 8: SG_CALL(8); break;   case 9: SG_CALL(9); break;
+    case 10: SG_CALL(10); break; case 11: SG_CALL(11); break; case 12: SG_CALL(12); break;
+    case 13: SG_CALL(13); break; case 14: SG_CALL(14); break; case 15: SG_CALL(15); break;
+    case 16: SG_CALL(16); break; default: return sg_fail(SG_ERR_INVALID, "extrap: bad term count");
+  }
+#undef SG_CALL
   SG_LAUNCH_CHECK("k_extrap");
   return SG_OK;
 }
