@@ -112,11 +112,18 @@ size_t sg_pcg_workspace_bytes(sg_op_t op);
  * solution on exit (Dirichlet entries set to 0).  tol > 0, maxit >= 0,
  * criterion from sg_criterion.  workspace: device, sg_pcg_workspace_bytes.
  * iters, relres: HOST outputs (may be NULL) -- the iteration count and the
- * final true relative residual ||b - A x|| / ||b||.  The call synchronises
- * with ``stream`` (the host polls convergence every few iterations).
- * Returns SG_OK, SG_NOT_CONVERGED (maxit reached) or SG_ERR_BREAKDOWN. */
+ * final true relative residual ||b - A x|| / ||b||; with relres NULL the
+ * extra operator application that measures the true residual is skipped.
+ * The call synchronises with ``stream`` (the host polls convergence once per
+ * chunk of iterations; the first chunk is sized from the previous solve with
+ * this operator).  Returns SG_OK, SG_NOT_CONVERGED (maxit reached) or
+ * SG_ERR_BREAKDOWN. */
 int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
                  void* workspace, int* iters, double* relres, void* stream);
+
+/* relres = ||b - A x|| / ||b|| (HOST output; Dirichlet entries ignored) using
+ * a PCG workspace of this operator.  Synchronises with ``stream``. */
+int sg_residual_norm(sg_op_t op, const void* b, const void* x, void* workspace, double* relres, void* stream);
 
 /* ------------------------------------------------------------------------
  * Mixed precision: FP32 operator, PCG vectors and history wrapped in FP64

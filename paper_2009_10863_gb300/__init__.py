@@ -41,6 +41,7 @@ SIGNATURES = [
     ("sg_sem_apply", _I, [_VP, _VP, _VP, _VP]),
     ("sg_op_diagonal", _I, [_VP, _VP, _VP]),
     ("sg_pcg_workspace_bytes", _SZ, [_VP]),
+    ("sg_residual_norm", _I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D), _VP]),
     ("sg_pcg_solve", _I, [_VP, _VP, _VP, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     ("sg_guess_workspace_bytes", _SZ, [_I64, _I, _I, _I]),
     ("sg_guess_create", _I, [ctypes.POINTER(_VP), _I64, _I, _I, _I, _D, _VP, _VP, _I]),
@@ -199,9 +200,9 @@ class Op:
             self._pcg_ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
         return self._pcg_ws
 
-    def pcg(self, b, x, tol, maxit=10000, criterion=STOP_REL_B, raise_on_maxit=False):
+    def pcg(self, b, x, tol, maxit=10000, criterion=STOP_REL_B, raise_on_maxit=False, true_residual=True):
         """Solve A x = b in place (x: initial guess in, solution out).
-        Returns (iterations, true relative residual)."""
+        Returns (iterations, true relative residual or None)."""
         self._vec(b, "b")
         self._vec(x, "x")
         ws = self.pcg_workspace()
@@ -209,8 +210,18 @@ class Op:
         rr = ctypes.c_double(0.0)
         allow = (OK,) if raise_on_maxit else (OK, NOT_CONVERGED)
         _check(lib().sg_pcg_solve(self.h, _ptr(b), _ptr(x), float(tol), int(maxit), int(criterion),
-                                  _ptr(ws), ctypes.byref(it), ctypes.byref(rr), _stream()), allow)
-        return it.value, rr.value
+                                  _ptr(ws), ctypes.byref(it), ctypes.byref(rr) if true_residual else None,
+                                  _stream()), allow)
+        return it.value, (rr.value if true_residual else None)
+
+    def residual_norm(self, b, x):
+        """||b - A x|| / ||b|| (synchronises)."""
+        self._vec(b, "b")
+        self._vec(x, "x")
+        rr = ctypes.c_double(0.0)
+        _check(lib().sg_residual_norm(self.h, _ptr(b), _ptr(x), _ptr(self.pcg_workspace()), ctypes.byref(rr),
+                                      _stream()))
+        return rr.value
 
 
 class Guess:

@@ -94,6 +94,7 @@ struct sg_op_s {
   FastDiv div_nx, div_nxy;
   int device;
   unsigned long long uid;   // unique per created operator (never reused)
+  int last_iters;           // iterations of the last PCG solve (sizes the first chunk)
 };
 
 // ---------------------------------------------------------------- reductions

@@ -244,12 +244,24 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
     if (!pinned) SG_CUDA_TRY(cudaHostAlloc((void**)&pinned, sizeof(PollBuf), cudaHostAllocDefault));
     poll = pinned;
   }
-  int launched = 0, chunk = 4;
+  // The first chunk is sized from the previous solve with this operator, so a
+  // sequence of similar solves usually needs one host poll per solve; the
+  // launches beyond convergence return at once.
+  int launched = 0;
+  int chunk = op->last_iters > 0 ? (op->last_iters < 64 ? op->last_iters + 1 : 64) : 4;
+  bool first_chunk = true;
   while (true) {
-    SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (poll->done) break;
-    if (launched >= maxit) break;   // defensive; the device sets done at maxit
+    if (!first_chunk) {
+      SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+      SG_CUDA_TRY(cudaStreamSynchronize(s));
+      if (poll->done) break;
+    }
+    first_chunk = false;
+    if (launched >= maxit) {                 // the device sets done at maxit
+      SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+      SG_CUDA_TRY(cudaStreamSynchronize(s));
+      break;
+    }
     const int k = (chunk < maxit - launched) ? chunk : (maxit - launched);
     for (int i = 0; i < k; ++i) {
       {
@@ -267,10 +279,10 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
       }
     }
     launched += k;
-    if (chunk < 16) chunk *= 2;
+    chunk = (chunk < 8) ? 8 : (chunk < 16 ? 16 : chunk);
   }
-  // true residual ||b - A x|| / ||b||
-  {
+  // true residual ||b - A x|| / ||b||, only when the caller asks for it
+  if (relres) {
     SemArgs<T> a{};
     a.x = x; a.aux = b; a.invd = invd; a.out = r; a.out2 = z;
     a.partials = partials; a.st = st; a.final_pass = 1;
@@ -281,12 +293,45 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   SG_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
   SG_CUDA_TRY(cudaStreamSynchronize(s));
   if (iters) *iters = hs.iter;
+  op->last_iters = hs.iter;
   if (relres) *relres = hs.bb > 0 ? sqrt(hs.rr_true / hs.bb) : sqrt(hs.rr_true);
   if (hs.status == PCG_BREAKDOWN) return sg_fail(SG_ERR_BREAKDOWN, "pcg: breakdown (p^T A p <= 0 or non-finite value)");
   if (hs.status == PCG_MAXIT || hs.status == PCG_RUNNING) {
     sg_set_error("pcg: maximum iteration count reached");
     return SG_NOT_CONVERGED;
   }
+  return SG_OK;
+}
+
+extern "C" int sg_residual_norm(sg_op_t op, const void* b, const void* x, void* workspace, double* relres,
+                                void* stream) {
+  if (!op || !b || !x || !workspace || !relres) return sg_fail(SG_ERR_INVALID, "residual_norm: NULL argument");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "residual_norm: workspace must be 256-byte aligned");
+  PcgLayout L = layout_for(op);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
+  cudaStream_t s = as_stream(stream);
+  k_pcg_setup<<<1, 32, 0, s>>>(st, 1.0, 0, SG_STOP_REL_B);
+  SG_LAUNCH_CHECK("k_pcg_setup");
+  int rc;
+  if (op->dtype == SG_F64) {
+    SemArgs<double> a{};
+    a.x = static_cast<const double*>(x); a.aux = static_cast<const double*>(b);
+    a.out = reinterpret_cast<double*>(ws + L.r);
+    a.partials = reinterpret_cast<double*>(ws + L.partials); a.st = st; a.final_pass = 1;
+    rc = sg_sem_launch<double, 2>(op->g, a, s, 0);
+  } else {
+    SemArgs<float> a{};
+    a.x = static_cast<const float*>(x); a.aux = static_cast<const float*>(b);
+    a.out = reinterpret_cast<float*>(ws + L.r);
+    a.partials = reinterpret_cast<double*>(ws + L.partials); a.st = st; a.final_pass = 1;
+    rc = sg_sem_launch<float, 2>(op->g, a, s, 0);
+  }
+  if (rc) return rc;
+  PcgState hs;
+  SG_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  *relres = hs.bb > 0 ? sqrt(hs.rr_true / hs.bb) : sqrt(hs.rr_true);
   return SG_OK;
 }
 
@@ -480,8 +525,7 @@ extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, d
     SG_LAUNCH_CHECK("k_convert");
     SG_CUDA_TRY(cudaMemsetAsync(d32, 0, sizeof(float) * (size_t)n, s));
     int it = 0;
-    double rin = 0.0;
-    rc = pcg_run<float>(op32, r32, d32, inner_tol, maxit_inner, SG_STOP_REL_B, ws + I.ws32, I.L32, &it, &rin, s);
+    rc = pcg_run<float>(op32, r32, d32, inner_tol, maxit_inner, SG_STOP_REL_B, ws + I.ws32, I.L32, &it, nullptr, s);
     if (rc < 0) return rc;
     inner_total += it;
     k_add_correction<<<nb, 256, 0, s>>>(x64, d32, n);

@@ -128,20 +128,28 @@ __device__ __forceinline__ T row_dot(const T (&u)[P + 1], const EOTab<T, P>& t) 
 }
 
 // Tables of direction d, multiplied by ``mul`` (1 for the scaled tables; 1/a_d
-// for the unscaled register copy used by the FP32 kernel).
+// for an unscaled copy).  ``dadd`` is added to the diagonal of C before the
+// split (the z tables carry the mass term c_m this way): rows 1..p-1 get dadd,
+// the shared rows 0 and p get dadd/2 each, so a shared node, which sums row 0
+// of its element and row p of the element below, gets dadd once.  The sum
+// keeps C centrosymmetric.
 template <typename T, int P>
-__host__ __device__ inline void build_eotab(const SemGeom& g, int d, double mul, EOTab<T, P>& t) {
+__host__ __device__ inline void build_eotab(const SemGeom& g, int d, double mul, EOTab<T, P>& t, double dadd = 0.0) {
   using TL = SemTile<P>;
   constexpr int H = TL::H;
+  double Cm[P + 1][P + 1];
+  for (int a = 0; a <= P; ++a)
+    for (int l = 0; l <= P; ++l)
+      Cm[a][l] = g.C[d][a][l] + ((a == l) ? ((a == 0 || a == P) ? 0.5 * dadd : dadd) : 0.0);
   for (int a = 0; a < TL::HE; ++a) {
     const int aa = (a < H) ? a : P / 2;
     for (int l = 0; l < H; ++l) {
-      t.ce[a][l] = (T)(mul * 0.5 * (g.C[d][aa][l] + g.C[d][aa][P - l]));
-      if (a < H) t.co[a][l] = (T)(mul * 0.5 * (g.C[d][aa][l] - g.C[d][aa][P - l]));
+      t.ce[a][l] = (T)(mul * 0.5 * (Cm[aa][l] + Cm[aa][P - l]));
+      if (a < H) t.co[a][l] = (T)(mul * 0.5 * (Cm[aa][l] - Cm[aa][P - l]));
     }
-    t.cm[a] = TL::MID ? (T)(mul * g.C[d][aa][P / 2]) : (T)0;
+    t.cm[a] = TL::MID ? (T)(mul * Cm[aa][P / 2]) : (T)0;
   }
-  for (int l = 0; l <= P; ++l) t.crow[l] = (T)(mul * g.C[d][P][l]);
+  for (int l = 0; l <= P; ++l) t.crow[l] = (T)(mul * Cm[P][l]);
 }
 
 // One direction's line product: FP64 reads the scaled table of the direction
@@ -202,7 +210,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
   __syncthreads();                               // shared memory of a previous item is free
-  if (tid < 3) build_eotab<T, P>(g, tid, 1.0, sTab[tid]);
+  if (tid < 3) build_eotab<T, P>(g, tid, 1.0, sTab[tid], tid == 2 ? g.cm : 0.0);   // mass term in z
   if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
   if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
@@ -241,7 +249,6 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   const bool col_in = (gx < g.nx - 1) && (gy < g.ny - 1);
   const bool col_int = col_in && gx > 0 && gy > 0;
   const T wxy = sW[ia] * sW[ib];
-  const T cm = (T)g.cm;
   const size_t colbase = (size_t)gx + (size_t)g.nx * gy;
 
   // prologue: stage the first layer (all p+1 planes)
@@ -290,7 +297,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T o[P + 1];
       dir_line<T, P, CREG>(u, o, sTab[2], rt, sz);
 #pragma unroll
-      for (int c = 0; c < P; ++c) acc[c] = o[c] + cm * u[c];
+      for (int c = 0; c < P; ++c) acc[c] = o[c];   // includes c_m u (folded into the z tables)
       acc[0] += carry;
       carry = o[P];
     }
