@@ -12,6 +12,7 @@ one pass of the whole hot path over one right-hand side):
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -36,7 +37,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
-PCG_APPLY_TRAFFIC = 33920512 + 0
+PCG_APPLY_TRAFFIC = 33920256 + 0
 
 
 def aggregate_max(value, dist, device):
@@ -80,17 +81,26 @@ class Clocks:
         self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
+        """Start sampling every 50 ms; returns once the first sample is written."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 10 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+        self.window = None
+
+    def mark(self, t0, t1):
+        """Host wall-clock interval of the timed region."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -101,24 +111,25 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], None, set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(parts[1]), float(parts[2]),
+                             [nm for nm, v in zip(names, parts[5:9]) if v.lower().startswith("active")]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        inside = [r for r in rows if self.window and self.window[0] - 0.05 <= r[0] <= self.window[1] + 0.05]
+        use = inside or rows
+        if not use:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2],
+                "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
+                "window": "timed region" if inside else "whole run"}
 
 
 # ------------------------------------------------------------------ workload
@@ -182,7 +193,7 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
         g.form(None, slot)
         if mode == "ir":
             sg.convert(slot, x64)
-            o, i, r = ms.solve(b, x64, tol, inner_tol=1e-5)
+            o, i, r = ms.solve(b, x64, tol)
             sg.convert(x64, slot)
             outs.append(o)
         else:
@@ -251,11 +262,11 @@ def run_batched(sg, torch, device, steps, warmup, flush, mode, tune=True):
             g.form(b32s[i] if slot is None else None, x0)
             sg.convert(x0, x64s[i])
         if mode == "batched":
-            outer, inner, rel = solver.solve(bs, x64s, tol, inner_tol=1e-5)
+            outer, inner, rel = solver.solve(bs, x64s, tol)
         else:
             outer, inner, rel = [], [], []
             for i, ms in enumerate(solvers):
-                o, ii, r = ms.solve(bs[i], x64s[i], tol, inner_tol=1e-5)
+                o, ii, r = ms.solve(bs[i], x64s[i], tol)
                 outer.append(o); inner.append(ii); rel.append(r)
         for i, (g, op32) in enumerate(guesses):
             slot = g.next_slot()
@@ -294,6 +305,9 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
         host_x = torch.empty(op.n, dtype=torch.float64).pin_memory()
         dev_b = op.empty()
     launches = 0
+    if clocks:
+        clocks.start()
+    t_timed = None
     for k in range(warmup + steps):
         timed = k >= warmup
         if timed and k == warmup:
@@ -301,8 +315,7 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
             if prof:
                 sg.profile_reset()
                 sg.profile_enable(True)
-            if clocks:
-                clocks.start()
+            t_timed = time.time()
             launches = sg.launch_count()
         if timed:
             ev[k - warmup][0].record()
@@ -330,6 +343,8 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
     launches = sg.launch_count() - launches
     if prof:
         sg.profile_enable(False)
+    if clocks:
+        clocks.mark(t_timed, time.time())
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
     return {"ms": ms, "iters": iters, "rels": rels, "launches": launches, "clocks": clk}

@@ -142,8 +142,10 @@ size_t sg_ir_workspace_bytes(sg_op_t op64, sg_op_t op32);
  * and op32 (SG_F32) must describe the same mesh, degree and lambda.  b, x:
  * FP64 device vectors (x: initial guess in, solution out; Dirichlet entries
  * set to 0).  Each outer step forms r = b - A x in FP64, solves A d = r with
- * FP32 Jacobi-PCG to ||r_inner|| <= inner_tol ||r|| (at most maxit_inner
- * iterations, from d = 0) and adds x += d in FP64, until the FP64 residual
+ * FP32 Jacobi-PCG to ||r_inner|| <= t ||r|| (at most maxit_inner iterations,
+ * from d = 0), t = min(0.1, max(inner_tol, tol ||b|| / (2 ||r||))) -- a step
+ * is not solved tighter than the outer target needs -- and adds x += d in
+ * FP64, until the FP64 residual
  * meets tol or max_outer steps were taken.  outer_iters, inner_iters (total
  * FP32 PCG iterations), relres: HOST outputs, may be NULL.  Synchronises
  * with ``stream`` once per outer step.  Returns SG_OK, SG_NOT_CONVERGED
@@ -177,7 +179,8 @@ int sg_batch_tune(sg_batch_t b, int* best_zl, int* best_blocks_per_sm, double* b
 /* Solve A_k x_k = b_k for every system k to ||b_k - A_k x_k|| <= tol ||b_k||
  * (FP64 residuals).  bvec[k], xvec[k]: FP64 device vectors (x: initial guess
  * in, solution out).  Per outer step: FP64 residual of every unconverged
- * system, one batched FP32 PCG solve to inner_tol (relative), x += d.
+ * system, one batched FP32 PCG solve (system k to the relative tolerance t_k
+ * that sg_ir_solve uses, from its own residual), x += d.
  * outer_iters, inner_iters, relres: HOST arrays of nseq (may be NULL).
  * Synchronises.  Returns SG_OK, SG_NOT_CONVERGED, SG_ERR_TIMEOUT (a grid
  * barrier wait expired) or another negative error. */

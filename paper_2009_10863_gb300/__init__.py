@@ -301,7 +301,7 @@ class MixedSolver:
         nb = int(lib().sg_ir_workspace_bytes(self.op64.h, self.op32.h))
         self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
 
-    def solve(self, b, x, tol, inner_tol=1e-5, max_outer=30, maxit_inner=10000):
+    def solve(self, b, x, tol, inner_tol=1e-4, max_outer=30, maxit_inner=10000):
         """Solve in place; returns (outer steps, total inner FP32 iterations, FP64 relres)."""
         self.op64._vec(b, "b")
         self.op64._vec(x, "x")
@@ -344,7 +344,7 @@ class BatchSolver:
         _check(lib().sg_batch_tune(self.h, ctypes.byref(zl), ctypes.byref(bps), ctypes.byref(ms), _stream()))
         return zl.value, bps.value, ms.value
 
-    def solve(self, bs, xs, tol, inner_tol=1e-5, max_outer=30, maxit_inner=10000):
+    def solve(self, bs, xs, tol, inner_tol=1e-4, max_outer=30, maxit_inner=10000):
         """Solve every system in place.  Returns (outer, inner, relres) lists."""
         k = self.k
         for o, b, x in zip(self.ops64, bs, xs):

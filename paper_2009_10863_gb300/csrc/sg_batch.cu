@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
 
 // Start of a batched inner solve from x = 0: r = b, z = r / diag(A),
 // r.r, r.z, b.b per system; blockIdx.y selects the system.
-__global__ void __launch_bounds__(256) k_batch_init(const __grid_constant__ BatchArgs A, double tol_rel, int maxit, unsigned int* counters,
+struct BatchTol { double rel[SG_BATCH_MAX]; };
+
+__global__ void __launch_bounds__(256) k_batch_init(const __grid_constant__ BatchArgs A, BatchTol tol, int maxit, unsigned int* counters,
                                                     const int* active) {
   __shared__ double sred[32 * 3];
   const int s = blockIdx.y;
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(256) k_batch_init(const __grid_constant__ Batc
     counters[s] = 0u;
     PcgState* st = S.st;
     st->rr = acc[0]; st->rz = acc[1]; st->bb = acc[2]; st->rr0 = acc[0];
-    st->thr2 = tol_rel * tol_rel * acc[2];
+    st->thr2 = tol.rel[s] * tol.rel[s] * acc[2];
     st->iter = 0; st->first = 1; st->beta = 0.0; st->maxit = maxit;
     st->status = PCG_RUNNING; st->done = 0;
     if (!isfinite(acc[0])) { st->status = PCG_BREAKDOWN; st->done = 1; }
@@ -525,12 +527,12 @@ extern "C" int sg_batch_destroy(sg_batch_t b) {
 
 // Inner batched FP32 PCG on the systems flagged active (b: the FP32 right-hand
 // sides already in the workspace).  Per-system iteration counts out.
-static int batch_inner(sg_batch_t b, const int* active, double tol_rel, int maxit, int* iters, cudaStream_t s) {
+static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int maxit, int* iters, cudaStream_t s) {
   BatchArgs A = make_args(b);
   SG_CUDA_TRY(cudaMemcpyAsync(b->ws + b->off_active, active, sizeof(int) * b->nseq, cudaMemcpyHostToDevice, s));
   int gx = 4 * sg_num_sms() / (b->nseq > 0 ? b->nseq : 1);
   if (gx < 1) gx = 1;
-  k_batch_init<<<dim3(gx, b->nseq), 256, 0, s>>>(A, tol_rel, maxit, reinterpret_cast<unsigned int*>(b->ws + b->off_counters),
+  k_batch_init<<<dim3(gx, b->nseq), 256, 0, s>>>(A, tol, maxit, reinterpret_cast<unsigned int*>(b->ws + b->off_counters),
                                                  reinterpret_cast<const int*>(b->ws + b->off_active));
   SG_LAUNCH_CHECK("k_batch_init");
   // graph of graph_iters persistent iterations, captured once per stream
@@ -627,7 +629,9 @@ extern "C" int sg_batch_ir_solve(sg_batch_t b, const void* const* bvec, void* co
     }
     if (!any) break;
     int it[SG_BATCH_MAX] = {0};
-    int rc = batch_inner(b, active, inner_tol, maxit_inner, it, s);
+    BatchTol itol{};
+    for (int k = 0; k < ns; ++k) itol.rel[k] = active[k] ? ir_inner_tol(inner_tol, tol, rel[k]) : inner_tol;
+    int rc = batch_inner(b, active, itol, maxit_inner, it, s);
     if (rc) return rc;
     for (int k = 0; k < ns; ++k) {
       if (!active[k]) continue;
@@ -686,7 +690,9 @@ extern "C" int sg_batch_tune(sg_batch_t b, int* best_zl, int* best_blocks_per_sm
       A = make_args(b);
       int gx = 4 * sg_num_sms() / b->nseq;
       cudaMemcpyAsync(b->ws + b->off_active, active, sizeof(int) * b->nseq, cudaMemcpyHostToDevice, s);
-      k_batch_init<<<dim3(gx > 0 ? gx : 1, b->nseq), 256, 0, s>>>(A, 1e-30, 1 << 30,
+      BatchTol none{};
+      for (int k = 0; k < SG_BATCH_MAX; ++k) none.rel[k] = 1e-30;
+      k_batch_init<<<dim3(gx > 0 ? gx : 1, b->nseq), 256, 0, s>>>(A, none, 1 << 30,
           reinterpret_cast<unsigned int*>(b->ws + b->off_counters), reinterpret_cast<const int*>(b->ws + b->off_active));
       sg_count_launch();
       for (int w = 0; w < 2; ++w) if ((rc = launch_iter(b, s))) break;

@@ -170,5 +170,8 @@ __device__ bool grid_reduce_last(double (&v)[NV], double* partials, unsigned int
 
 // ---------------------------------------------------------------- launch helpers
 int sg_num_sms();
+// Relative tolerance of one FP32 inner solve of iterative refinement given
+// the outer target tol and the current relative FP64 residual rel.
+double ir_inner_tol(double inner_tol, double tol, double rel);
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -481,6 +481,16 @@ extern "C" size_t sg_ir_workspace_bytes(sg_op_t op64, sg_op_t op32) {
   return ir_layout(op64, op32).total;
 }
 
+// Relative tolerance of one inner solve.  A correction that reduces the
+// current residual (relative size rel) by tol / rel already meets the outer
+// target, so the last outer step is not solved tighter than that (with a
+// factor 2 of margin); inner_tol is the floor and 0.1 the ceiling.
+double ir_inner_tol(double inner_tol, double tol, double rel) {
+  double t = 0.5 * tol / rel;
+  if (t < inner_tol) t = inner_tol;
+  return t < 0.1 ? t : (inner_tol > 0.1 ? inner_tol : 0.1);
+}
+
 extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double inner_tol,
                            int max_outer, int maxit_inner, void* workspace, int* outer_iters,
                            int* inner_iters, double* relres, void* stream) {
@@ -525,7 +535,8 @@ extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, d
     SG_LAUNCH_CHECK("k_convert");
     SG_CUDA_TRY(cudaMemsetAsync(d32, 0, sizeof(float) * (size_t)n, s));
     int it = 0;
-    rc = pcg_run<float>(op32, r32, d32, inner_tol, maxit_inner, SG_STOP_REL_B, ws + I.ws32, I.L32, &it, nullptr, s);
+    rc = pcg_run<float>(op32, r32, d32, ir_inner_tol(inner_tol, tol, rel), maxit_inner, SG_STOP_REL_B, ws + I.ws32,
+                        I.L32, &it, nullptr, s);
     if (rc < 0) return rc;
     inner_total += it;
     k_add_correction<<<nb, 256, 0, s>>>(x64, d32, n);
