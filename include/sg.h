@@ -114,12 +114,31 @@ size_t sg_pcg_workspace_bytes(sg_op_t op);
  * iters, relres: HOST outputs (may be NULL) -- the iteration count and the
  * final true relative residual ||b - A x|| / ||b||; with relres NULL the
  * extra operator application that measures the true residual is skipped.
- * The call synchronises with ``stream`` (the host polls convergence once per
- * chunk of iterations; the first chunk is sized from the previous solve with
- * this operator).  Returns SG_OK, SG_NOT_CONVERGED (maxit reached) or
- * SG_ERR_BREAKDOWN. */
+ * The call synchronises with ``stream`` once, at the end.  The iterations run
+ * as one CUDA graph launch (a conditional WHILE node over the operator step and
+ * the update, whose last block ends the loop on convergence, breakdown or
+ * maxit), built on first use per (operator, workspace address) and cached on
+ * the operator until sg_op_destroy.  While sg_profile_enable is on (each
+ * kernel timed), or if graphs cannot be built, the host launches the
+ * iterations in chunks and polls a done flag after each chunk.  Returns SG_OK,
+ * SG_NOT_CONVERGED (maxit reached) or SG_ERR_BREAKDOWN. */
 int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
                  void* workspace, int* iters, double* relres, void* stream);
+
+/* The same solve, enqueued on ``stream`` without waiting: set-up kernels and
+ * the iteration graph of sg_pcg_solve (no host poll, no synchronisation).  x
+ * and b must stay valid until the stream reaches that point; the outcome is
+ * read with sg_pcg_result on the same workspace before the next solve in it.
+ * No counterpart in the paper (Sec. 5.3's PCG, launched asynchronously).
+ * Returns SG_OK once enqueued, SG_ERR_INVALID, or SG_ERR_CUDA when the
+ * iteration graph cannot be built. */
+int sg_pcg_solve_async(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
+                       void* workspace, void* stream);
+
+/* Outcome of the last solve run in ``workspace``: iters (HOST, may be NULL);
+ * synchronises with ``stream``.  Returns SG_OK, SG_NOT_CONVERGED or
+ * SG_ERR_BREAKDOWN as sg_pcg_solve would have. */
+int sg_pcg_result(sg_op_t op, void* workspace, int* iters, void* stream);
 
 /* relres = ||b - A x|| / ||b|| (HOST output; Dirichlet entries ignored) using
  * a PCG workspace of this operator.  Synchronises with ``stream``. */

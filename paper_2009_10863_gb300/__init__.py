@@ -43,6 +43,8 @@ SIGNATURES = [
     ("sg_pcg_workspace_bytes", _SZ, [_VP]),
     ("sg_residual_norm", _I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D), _VP]),
     ("sg_pcg_solve", _I, [_VP, _VP, _VP, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    ("sg_pcg_solve_async", _I, [_VP, _VP, _VP, _D, _I, _I, _VP, _VP]),
+    ("sg_pcg_result", _I, [_VP, _VP, ctypes.POINTER(_I), _VP]),
     ("sg_guess_workspace_bytes", _SZ, [_I64, _I, _I, _I]),
     ("sg_guess_create", _I, [ctypes.POINTER(_VP), _I64, _I, _I, _I, _D, _VP, _VP, _I]),
     ("sg_guess_destroy", _I, [_VP]),
@@ -213,6 +215,21 @@ class Op:
                                   _ptr(ws), ctypes.byref(it), ctypes.byref(rr) if true_residual else None,
                                   _stream()), allow)
         return it.value, (rr.value if true_residual else None)
+
+    def pcg_async(self, b, x, tol, maxit=10000, criterion=STOP_REL_B):
+        """Enqueue the solve of A x = b on the current stream without waiting;
+        read the outcome with ``pcg_result`` before the next solve."""
+        self._vec(b, "b")
+        self._vec(x, "x")
+        _check(lib().sg_pcg_solve_async(self.h, _ptr(b), _ptr(x), float(tol), int(maxit), int(criterion),
+                                        _ptr(self.pcg_workspace()), _stream()))
+
+    def pcg_result(self, raise_on_maxit=False):
+        """Iteration count of the last solve (waits for it)."""
+        it = ctypes.c_int(0)
+        allow = (OK,) if raise_on_maxit else (OK, NOT_CONVERGED)
+        _check(lib().sg_pcg_result(self.h, _ptr(self.pcg_workspace()), ctypes.byref(it), _stream()), allow)
+        return it.value
 
     def residual_norm(self, b, x):
         """||b - A x|| / ||b|| (synchronises)."""

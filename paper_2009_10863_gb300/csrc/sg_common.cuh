@@ -22,6 +22,7 @@ int sg_fail(int code, const std::string& msg);
   } while (0)
 
 void sg_count_launch();
+void sg_count_launches(long long n);   // kernels a graph launch ran
 
 #define SG_LAUNCH_CHECK(name)                                                    \
   do {                                                                          \
@@ -95,7 +96,13 @@ struct sg_op_s {
   int device;
   unsigned long long uid;   // unique per created operator (never reused)
   int last_iters;           // iterations of the last PCG solve (sizes the first chunk)
+  void* pcg_graphs;         // cached PCG iteration graphs (sg_pcg.cu), released with the operator
 };
+
+// Release the PCG iteration graphs cached on an operator (sg_pcg.cu).
+void sg_pcg_release(sg_op_s* op);
+// True while library-side kernel timing is enabled (sg_profile_enable).
+bool sg_profiling_on();
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
@@ -131,6 +138,42 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32
   __syncthreads();
 }
 
+// Deterministic block sum of two values per thread with half the FP64
+// additions of two separate shuffle trees: one exchange at distance 16 leaves
+// partial sums of a in lanes 0-15 and of b in lanes 16-31, and four more rounds
+// reduce one value per lane.  Blocks of at most 512 threads.  Results valid in
+// thread 0 (a and b).
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* smem /* >= 64 */) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+  const int tl = tid & 31, tw = tid >> 5;
+  const bool hi = (tl & 16) != 0;
+  double keep = hi ? b : a;
+  const double give = hi ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, give, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  __syncthreads();
+  if (tl == 0) smem[tw] = keep;             // warp sum of a
+  if (tl == 16) smem[32 + tw] = keep;       // warp sum of b
+  __syncthreads();
+  if (tw == 0) {
+    const int w = tl & 15;
+    double x = (w < nwarps) ? smem[(hi ? 32 : 0) + w] : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const double xb = __shfl_sync(0xffffffffu, x, 16);
+    if (tl == 0) { a = x; b = xb; }
+  }
+  __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_any(double (&v)[NV], double* smem) {
+  if constexpr (NV == 2) block_sum2(v[0], v[1], smem);
+  else block_sum<NV>(v, smem);
+}
+
 // Grid-level deterministic reduction: every block writes its NV partial sums
 // to partials[block*NV + k]; the last block to finish sums them in block
 // order and returns true (in all of its threads) with the totals in out[]
@@ -143,7 +186,7 @@ __device__ bool grid_reduce_last(double (&v)[NV], double* partials, unsigned int
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_sum<NV>(v, smem);
+  block_sum_any<NV>(v, smem);
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
@@ -161,7 +204,7 @@ __device__ bool grid_reduce_last(double (&v)[NV], double* partials, unsigned int
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partials[(size_t)b * NV + k]);
   }
-  block_sum<NV>(acc, smem);
+  block_sum_any<NV>(acc, smem);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = acc[k];
   if (tid == 0) *counter = 0u;

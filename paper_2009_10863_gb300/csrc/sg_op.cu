@@ -23,6 +23,7 @@ extern "C" int sg_version(void) { return 1; }
 
 static std::atomic<long long> g_launches{0};
 void sg_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void sg_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 extern "C" long long sg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int sg_num_sms() {
@@ -82,6 +83,7 @@ ProfScope::~ProfScope() {
 }
 
 extern "C" int sg_profile_enable(int on) { g_prof_on = (on != 0); return SG_OK; }
+bool sg_profiling_on() { return g_prof_on; }
 extern "C" int sg_profile_reset(void) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_drain();
@@ -173,6 +175,7 @@ extern "C" int sg_op_create(sg_op_t* out, int ex, int ey, int ez, int p, double 
 }
 
 extern "C" int sg_op_destroy(sg_op_t op) {
+  if (op) sg_pcg_release(op);
   delete op;
   return SG_OK;
 }

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "sg_sem_launch.cuh"
 
@@ -27,10 +28,15 @@ struct PcgLayout {
   int max_blocks;
 };
 
+// Grid of the update kernel.  FP64 (vec 2): 2 CTAs of 256 per SM -- its cost
+// is FP64 instructions, and each block's r.r / r.z reduction adds FP64 work in
+// proportion to the block count (8 CTAs per SM: 1.2 additions per node on the
+// 16^3 p = 7 mesh, 2 per SM: 0.3; measured 3.32 -> 3.72 TB/s there).  FP32
+// (vec 4): 8 per SM, a full wave, for memory-level parallelism.
 int update_blocks(int64_t n, int vec) {
   int64_t nv = (n + vec - 1) / vec;
   int64_t b = (nv + 255) / 256;
-  int64_t cap = 8LL * sg_num_sms();
+  int64_t cap = (vec == 2 ? 2LL : 8LL) * sg_num_sms();
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -117,12 +123,13 @@ __global__ void k_set_diag_tag(PcgState* st, unsigned long long tag) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->diag_tag = tag;
 }
 
-__global__ void k_pcg_setup(PcgState* st, double tol, int maxit, int criterion) {
+__global__ void k_pcg_setup(PcgState* st, double tol, int maxit, int criterion, void* x) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     st->rz = st->pq = st->rr = st->bb = st->rr0 = st->thr2 = 0.0;
     st->alpha = st->beta = st->rr_true = 0.0;
     st->iter = 0; st->done = 0; st->status = PCG_RUNNING; st->first = 1;
     st->maxit = maxit; st->criterion = criterion; st->tol = tol;
+    st->xvec = x;
     for (int i = 0; i < 4; ++i) st->counter[i] = 0u;
   }
 }
@@ -140,18 +147,28 @@ __device__ __forceinline__ void upd1(T& x, T p, T& r, T q, T id, T& z, T al, T& 
   rz += r * z;
 }
 
+// x == NULL: the solution vector recorded in the state by k_pcg_setup (the
+// form captured in the iteration graph).  use_cond: the launch is a node of the
+// graph's WHILE body; the last block (or, once the solve is done, block 0)
+// sets the loop condition to "not done".
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_pcg_update(T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r, const T* __restrict__ q,
-             const T* __restrict__ invd, T* __restrict__ z, int n, PcgState* st, double* partials) {
+k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, const T* __restrict__ q,
+             const T* __restrict__ invd, T* __restrict__ z, int n, PcgState* st, double* partials,
+             cudaGraphConditionalHandle cond, int use_cond) {
   using V = typename Vec<T>::V;
   constexpr int W = Vec<T>::W;
   __shared__ int s_skip;
   __shared__ double s_alpha;
+  __shared__ T* s_x;
   __shared__ double sred[64];
-  if (threadIdx.x == 0) { s_skip = st->done; s_alpha = st->alpha; }
+  if (threadIdx.x == 0) { s_skip = st->done; s_alpha = st->alpha; s_x = x_arg ? x_arg : static_cast<T*>(st->xvec); }
   __syncthreads();
-  if (s_skip) return;
+  if (s_skip) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  T* __restrict__ x = s_x;
   const T al = (T)s_alpha;
   T rr = 0, rz = 0;
   const int nv = n / W;
@@ -192,6 +209,7 @@ k_pcg_update(T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r, cons
         st->rz = tot[1];
         if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
       }
+      if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
     }
   }
 }
@@ -203,9 +221,30 @@ struct MaybeProf { MaybeProf(int, cudaStream_t) {} };
 template <>
 struct MaybeProf<true> { ProfScope ps; MaybeProf(int id, cudaStream_t s) : ps(id, s) {} };
 
-template <typename T, bool NOALLOC = false>
-static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion,
-                   unsigned char* ws, const PcgLayout& L, int* iters, double* relres, cudaStream_t s) {
+// ---------------------------------------------------------------- device-driven iterations
+// The iterations of a solve can run as one CUDA graph: a conditional WHILE node
+// whose body is the operator step (k_sem MODE 1) followed by the update
+// (k_pcg_update), which sets the loop condition to "not done" after every
+// iteration.  No host poll and no per-iteration launch: the host enqueues the
+// set-up kernels and one graph launch.  The graph references only the
+// workspace (the solution vector is taken from the PCG state), so it is built
+// once per (operator, workspace address) and cached on the operator.
+namespace {
+struct PcgGraphEntry { const void* ws; cudaGraphExec_t exec; };
+struct PcgGraphCache {
+  std::vector<PcgGraphEntry> entries;   // most recent last
+  bool unavailable = false;             // graph construction failed once: use launches
+  std::string why;
+};
+constexpr size_t kGraphCacheMax = 8;
+
+PcgGraphCache* graph_cache(sg_op_t op) {
+  if (!op->pcg_graphs) op->pcg_graphs = new PcgGraphCache();
+  return static_cast<PcgGraphCache*>(op->pcg_graphs);
+}
+
+template <typename T>
+int build_iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L, cudaGraphExec_t* out) {
   PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
   double* partials = reinterpret_cast<double*>(ws + L.partials);
   T* r = reinterpret_cast<T*>(ws + L.r);
@@ -214,8 +253,96 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   T* q = reinterpret_cast<T*>(ws + L.q);
   T* invd = reinterpret_cast<T*>(ws + L.invd);
   const int n = (int)op->n;
-  const SemGeom& g = op->g;
+  int rc = sg_sem_prepare<T, 1>(op->g);
+  if (rc) return rc;
+  cudaGraph_t graph = nullptr, body = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams cp = {};
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess) {
+    body = cp.conditional.phGraph_out[0];
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    SemArgs<T> a{};
+    a.x = z; a.out = q; a.out2 = p;
+    a.partials = partials; a.st = st;
+    rc = sg_sem_launch<T, 1>(op->g, a, cs, 0);
+    if (rc == SG_OK) {
+      k_pcg_update<T><<<update_blocks(op->n, Vec<T>::W), 256, 0, cs>>>(nullptr, p, r, q, invd, z, n, st, partials,
+                                                                    cond, 1);
+      e = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && rc == SG_OK) e = cudaGraphInstantiate(out, graph, 0);
+  if (cs) cudaStreamDestroy(cs);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc) return rc;
+  if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("pcg iteration graph: ") + cudaGetErrorString(e));
+  return SG_OK;
+}
 
+// The cached graph for (op, ws), built on first use; NULL (and the reason in
+// the cache) when graphs cannot be built on this device.
+template <typename T>
+cudaGraphExec_t iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L) {
+  PcgGraphCache* c = graph_cache(op);
+  if (c->unavailable) return nullptr;
+  for (size_t i = 0; i < c->entries.size(); ++i) {
+    if (c->entries[i].ws == ws) {
+      PcgGraphEntry hit = c->entries[i];
+      c->entries.erase(c->entries.begin() + (long)i);
+      c->entries.push_back(hit);
+      return hit.exec;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (build_iteration_graph<T>(op, ws, L, &exec) != SG_OK) {
+    c->unavailable = true;
+    c->why = sg_last_error();
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (c->entries.size() >= kGraphCacheMax) {
+    cudaGraphExecDestroy(c->entries.front().exec);   // freed after any launch in flight completes
+    c->entries.erase(c->entries.begin());
+  }
+  c->entries.push_back({ws, exec});
+  return exec;
+}
+}  // namespace
+
+void sg_pcg_release(sg_op_s* op) {
+  if (!op || !op->pcg_graphs) return;
+  PcgGraphCache* c = static_cast<PcgGraphCache*>(op->pcg_graphs);
+  for (auto& en : c->entries) cudaGraphExecDestroy(en.exec);
+  delete c;
+  op->pcg_graphs = nullptr;
+}
+
+// Set-up of a solve on the stream: 1/diag(A) (unless cached), Dirichlet
+// entries of x to 0, state reset, r = b - A x, z = r / diag(A), r.r, r.z, b.b.
+template <typename T>
+static int pcg_start(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion, unsigned char* ws,
+                     const PcgLayout& L, cudaStream_t s) {
+  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
+  T* invd = reinterpret_cast<T*>(ws + L.invd);
+  const int n = (int)op->n;
+  const SemGeom& g = op->g;
   {
     const unsigned long long tag = diag_tag(op);
     int blocks = (n + 255) / 256;
@@ -227,15 +354,30 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   }
   k_mask_faces<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz);
   SG_LAUNCH_CHECK("k_mask_faces");
-  k_pcg_setup<<<1, 32, 0, s>>>(st, tol, maxit, criterion);
+  k_pcg_setup<<<1, 32, 0, s>>>(st, tol, maxit, criterion, x);
   SG_LAUNCH_CHECK("k_pcg_setup");
-  {
-    SemArgs<T> a{};
-    a.x = x; a.aux = b; a.invd = invd; a.out = r; a.out2 = z;
-    a.partials = partials; a.st = st; a.final_pass = 0;
-    int rc = sg_sem_launch<T, 2>(g, a, s, 0);
-    if (rc) return rc;
-  }
+  SemArgs<T> a{};
+  a.x = x; a.aux = b; a.invd = invd; a.out = reinterpret_cast<T*>(ws + L.r); a.out2 = reinterpret_cast<T*>(ws + L.z);
+  a.partials = reinterpret_cast<double*>(ws + L.partials); a.st = st; a.final_pass = 0;
+  return sg_sem_launch<T, 2>(g, a, s, 0);
+}
+
+// Iterations by host launches: chunks of (operator step, update) pairs, the
+// done flag read after each chunk.  The first chunk is sized from the previous
+// solve with this operator, so a sequence of similar solves usually needs one
+// poll; launches beyond convergence return at once.  Used when kernels are
+// timed one by one (sg_profile_enable), by the allocation-free entry point,
+// and where graphs cannot be built.
+template <typename T, bool NOALLOC>
+static int pcg_iterate_launches(sg_op_t op, T* x, int maxit, unsigned char* ws, const PcgLayout& L, cudaStream_t s) {
+  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
+  double* partials = reinterpret_cast<double*>(ws + L.partials);
+  T* r = reinterpret_cast<T*>(ws + L.r);
+  T* z = reinterpret_cast<T*>(ws + L.z);
+  T* p = reinterpret_cast<T*>(ws + L.p);
+  T* q = reinterpret_cast<T*>(ws + L.q);
+  T* invd = reinterpret_cast<T*>(ws + L.invd);
+  const int n = (int)op->n;
   const int ub = update_blocks(op->n, Vec<T>::W);
   PollBuf local_poll{};      // pageable host memory: no pinned allocation
   PollBuf* poll = &local_poll;
@@ -244,9 +386,6 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
     if (!pinned) SG_CUDA_TRY(cudaHostAlloc((void**)&pinned, sizeof(PollBuf), cudaHostAllocDefault));
     poll = pinned;
   }
-  // The first chunk is sized from the previous solve with this operator, so a
-  // sequence of similar solves usually needs one host poll per solve; the
-  // launches beyond convergence return at once.
   int launched = 0;
   int chunk = op->last_iters > 0 ? (op->last_iters < 64 ? op->last_iters + 1 : 64) : 4;
   bool first_chunk = true;
@@ -257,11 +396,7 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
       if (poll->done) break;
     }
     first_chunk = false;
-    if (launched >= maxit) {                 // the device sets done at maxit
-      SG_CUDA_TRY(cudaMemcpyAsync(poll, &st->iter, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
-      SG_CUDA_TRY(cudaStreamSynchronize(s));
-      break;
-    }
+    if (launched >= maxit) break;            // the device sets done at maxit
     const int k = (chunk < maxit - launched) ? chunk : (maxit - launched);
     for (int i = 0; i < k; ++i) {
       {
@@ -269,29 +404,40 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
         SemArgs<T> a{};
         a.x = z; a.out = q; a.out2 = p;
         a.partials = partials; a.st = st;
-        int rc = sg_sem_launch<T, 1>(g, a, s, 0);
+        int rc = sg_sem_launch<T, 1>(op->g, a, s, 0);
         if (rc) return rc;
       }
       {
         MaybeProf<!NOALLOC> ps(PROF_PCG_UPDATE, s);
-        k_pcg_update<T><<<ub, 256, 0, s>>>(x, p, r, q, invd, z, n, st, partials);
+        k_pcg_update<T><<<ub, 256, 0, s>>>(x, p, r, q, invd, z, n, st, partials, 0, 0);
         SG_LAUNCH_CHECK("k_pcg_update");
       }
     }
     launched += k;
     chunk = (chunk < 8) ? 8 : (chunk < 16 ? 16 : chunk);
   }
-  // true residual ||b - A x|| / ||b||, only when the caller asks for it
+  return SG_OK;
+}
+
+// Outcome of the solve in this workspace (synchronises): iteration count,
+// status, and with relres the true relative residual ||b - A x|| / ||b||
+// (one more operator pass).
+template <typename T>
+static int pcg_finish(sg_op_t op, const T* b, T* x, unsigned char* ws, const PcgLayout& L, int* iters,
+                      double* relres, cudaStream_t s, bool count_graph_launches) {
+  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
   if (relres) {
     SemArgs<T> a{};
-    a.x = x; a.aux = b; a.invd = invd; a.out = r; a.out2 = z;
-    a.partials = partials; a.st = st; a.final_pass = 1;
-    int rc = sg_sem_launch<T, 2>(g, a, s, 0);
+    a.x = x; a.aux = b; a.invd = reinterpret_cast<T*>(ws + L.invd);
+    a.out = reinterpret_cast<T*>(ws + L.r); a.out2 = reinterpret_cast<T*>(ws + L.z);
+    a.partials = reinterpret_cast<double*>(ws + L.partials); a.st = st; a.final_pass = 1;
+    int rc = sg_sem_launch<T, 2>(op->g, a, s, 0);
     if (rc) return rc;
   }
   PcgState hs;
   SG_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
   SG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (count_graph_launches) sg_count_launches(2 * (hs.iter > 0 ? hs.iter : 1));   // body kernels the graph ran
   if (iters) *iters = hs.iter;
   op->last_iters = hs.iter;
   if (relres) *relres = hs.bb > 0 ? sqrt(hs.rr_true / hs.bb) : sqrt(hs.rr_true);
@@ -303,6 +449,22 @@ static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int crit
   return SG_OK;
 }
 
+template <typename T, bool NOALLOC = false>
+static int pcg_run(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion,
+                   unsigned char* ws, const PcgLayout& L, int* iters, double* relres, cudaStream_t s) {
+  int rc = pcg_start<T>(op, b, x, tol, maxit, criterion, ws, L, s);
+  if (rc) return rc;
+  cudaGraphExec_t exec = nullptr;
+  if (!NOALLOC && !sg_profiling_on()) exec = iteration_graph<T>(op, ws, L);
+  if (exec) {
+    SG_CUDA_TRY(cudaGraphLaunch(exec, s));
+  } else {
+    rc = pcg_iterate_launches<T, NOALLOC>(op, x, maxit, ws, L, s);
+    if (rc) return rc;
+  }
+  return pcg_finish<T>(op, b, x, ws, L, iters, relres, s, exec != nullptr);
+}
+
 extern "C" int sg_residual_norm(sg_op_t op, const void* b, const void* x, void* workspace, double* relres,
                                 void* stream) {
   if (!op || !b || !x || !workspace || !relres) return sg_fail(SG_ERR_INVALID, "residual_norm: NULL argument");
@@ -311,7 +473,7 @@ extern "C" int sg_residual_norm(sg_op_t op, const void* b, const void* x, void* 
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
   cudaStream_t s = as_stream(stream);
-  k_pcg_setup<<<1, 32, 0, s>>>(st, 1.0, 0, SG_STOP_REL_B);
+  k_pcg_setup<<<1, 32, 0, s>>>(st, 1.0, 0, SG_STOP_REL_B, nullptr);
   SG_LAUNCH_CHECK("k_pcg_setup");
   int rc;
   if (op->dtype == SG_F64) {
@@ -335,6 +497,19 @@ extern "C" int sg_residual_norm(sg_op_t op, const void* b, const void* x, void* 
   return SG_OK;
 }
 
+static int pcg_check_args(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion, void* workspace,
+                          const char* who) {
+  const std::string w(who);
+  if (!op || !b || !x || !workspace) return sg_fail(SG_ERR_INVALID, w + ": NULL argument");
+  if (!(tol > 0.0)) return sg_fail(SG_ERR_INVALID, w + ": tol must be > 0");
+  if (maxit < 0) return sg_fail(SG_ERR_INVALID, w + ": maxit must be >= 0");
+  if (criterion < 0 || criterion > 2) return sg_fail(SG_ERR_INVALID, w + ": unknown criterion");
+  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, w + ": vectors must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, w + ": workspace must be 256-byte aligned");
+  if (b == x) return sg_fail(SG_ERR_INVALID, w + ": b and x must not alias");
+  return SG_OK;
+}
+
 extern "C" size_t sg_pcg_workspace_bytes(sg_op_t op) {
   if (!op) return 0;
   return layout_for(op).total;
@@ -342,13 +517,8 @@ extern "C" size_t sg_pcg_workspace_bytes(sg_op_t op) {
 
 extern "C" int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
                             void* workspace, int* iters, double* relres, void* stream) {
-  if (!op || !b || !x || !workspace) return sg_fail(SG_ERR_INVALID, "pcg_solve: NULL argument");
-  if (!(tol > 0.0)) return sg_fail(SG_ERR_INVALID, "pcg_solve: tol must be > 0");
-  if (maxit < 0) return sg_fail(SG_ERR_INVALID, "pcg_solve: maxit must be >= 0");
-  if (criterion < 0 || criterion > 2) return sg_fail(SG_ERR_INVALID, "pcg_solve: unknown criterion");
-  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, "pcg_solve: vectors must be 16-byte aligned");
-  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "pcg_solve: workspace must be 256-byte aligned");
-  if (b == x) return sg_fail(SG_ERR_INVALID, "pcg_solve: b and x must not alias");
+  int rc = pcg_check_args(op, b, x, tol, maxit, criterion, workspace, "pcg_solve");
+  if (rc) return rc;
   PcgLayout L = layout_for(op);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   cudaStream_t s = as_stream(stream);
@@ -357,6 +527,43 @@ extern "C" int sg_pcg_solve(sg_op_t op, const void* b, void* x, double tol, int 
                            criterion, ws, L, iters, relres, s);
   return pcg_run<float>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit,
                         criterion, ws, L, iters, relres, s);
+}
+
+template <typename T>
+static int pcg_enqueue(sg_op_t op, const T* b, T* x, double tol, int maxit, int criterion, unsigned char* ws,
+                       const PcgLayout& L, cudaStream_t s) {
+  cudaGraphExec_t exec = iteration_graph<T>(op, ws, L);
+  if (!exec)
+    return sg_fail(SG_ERR_CUDA, "pcg_solve_async: iteration graph unavailable: " +
+                                static_cast<PcgGraphCache*>(op->pcg_graphs)->why);
+  int rc = pcg_start<T>(op, b, x, tol, maxit, criterion, ws, L, s);
+  if (rc) return rc;
+  SG_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return SG_OK;
+}
+
+extern "C" int sg_pcg_solve_async(sg_op_t op, const void* b, void* x, double tol, int maxit, int criterion,
+                                  void* workspace, void* stream) {
+  int rc = pcg_check_args(op, b, x, tol, maxit, criterion, workspace, "pcg_solve_async");
+  if (rc) return rc;
+  PcgLayout L = layout_for(op);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  cudaStream_t s = as_stream(stream);
+  if (op->dtype == SG_F64)
+    return pcg_enqueue<double>(op, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit, criterion,
+                               ws, L, s);
+  return pcg_enqueue<float>(op, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit, criterion, ws, L, s);
+}
+
+extern "C" int sg_pcg_result(sg_op_t op, void* workspace, int* iters, void* stream) {
+  if (!op || !workspace) return sg_fail(SG_ERR_INVALID, "pcg_result: NULL argument");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "pcg_result: workspace must be 256-byte aligned");
+  PcgLayout L = layout_for(op);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  cudaStream_t s = as_stream(stream);
+  if (op->dtype == SG_F64)
+    return pcg_finish<double>(op, nullptr, nullptr, ws, L, iters, nullptr, s, true);
+  return pcg_finish<float>(op, nullptr, nullptr, ws, L, iters, nullptr, s, true);
 }
 
 // ---------------------------------------------------------------- allocation-free PCG
@@ -520,7 +727,7 @@ extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, d
   double rel = 0.0;
   PcgState hs;
   while (true) {
-    k_pcg_setup<<<1, 32, 0, s>>>(st, tol, 0, SG_STOP_REL_B);
+    k_pcg_setup<<<1, 32, 0, s>>>(st, tol, 0, SG_STOP_REL_B, nullptr);
     SG_LAUNCH_CHECK("k_pcg_setup");
     SemArgs<double> a{};
     a.x = x64; a.aux = b64; a.out = r64; a.partials = partials; a.st = st; a.final_pass = 1;

@@ -3,3 +3,4 @@
 template int sg_sem_launch<float, 0>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);
 template int sg_sem_launch<float, 1>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);
 template int sg_sem_launch<float, 2>(const SemGeom&, const SemArgs<float>&, cudaStream_t, int);
+template int sg_sem_prepare<float, 1>(const SemGeom&);

@@ -3,3 +3,4 @@
 template int sg_sem_launch<double, 0>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
 template int sg_sem_launch<double, 1>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
 template int sg_sem_launch<double, 2>(const SemGeom&, const SemArgs<double>&, cudaStream_t, int);
+template int sg_sem_prepare<double, 1>(const SemGeom&);

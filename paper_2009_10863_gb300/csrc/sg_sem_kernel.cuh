@@ -48,6 +48,7 @@ struct PcgState {
   double tol;
   unsigned int counter[4];
   unsigned long long diag_tag;   // operator tag of the 1/diag(A) held in the workspace
+  void* xvec;                    // solution vector of the running solve (set by the set-up kernel)
   int pad[6];
 };
 

@@ -499,3 +499,91 @@ def test_largest_history(sg, method):
         x0 = op.zeros()
         g.form(dev(b), x0)
         assert rel(host(x0), o.form(b, np.zeros(ref.n))) <= 1e-12
+
+
+# ---------------------------------------------------------------- device-driven PCG iterations
+def _pcg_problem(seed=50):
+    ref, rng, xs = _problem((4, 3, 3), 5, 20.0, seed=seed)
+    b = ref.apply(xs) + 0.01 * rng.standard_normal(ref.n) * ref.interior
+    x0 = 0.1 * rng.standard_normal(ref.n) * ref.interior
+    return ref, b, x0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_pcg_graph_launch_and_async_paths_agree(sg, dtype):
+    """The iteration graph (default), the host-launched chunks (taken while kernel
+    timing is on) and the asynchronous entry run the same kernels in the same
+    order: identical iterates and iteration counts; the FP64 one against the oracle."""
+    ref, b, x0 = _pcg_problem()
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-10 if dtype == "f64" else 1e-5
+    op = sg.Op(4, 3, 3, 5, 20.0, dtype)
+    bd = dev(b, tdt)
+    xg = dev(x0, tdt)
+    itg, _ = op.pcg(bd, xg, tol, true_residual=False)
+    sg.profile_enable(True)
+    try:
+        xl = dev(x0, tdt)
+        itl, _ = op.pcg(bd, xl, tol, true_residual=False)
+    finally:
+        sg.profile_enable(False)
+    xa = dev(x0, tdt)
+    op.pcg_async(bd, xa, tol)
+    ita = op.pcg_result()
+    assert itg == itl == ita and itg > 3
+    assert torch.equal(xg, xl) and torch.equal(xg, xa)
+    if dtype == "f64":
+        xo, ito, _, _ = opcg(ref.apply, ref.diagonal(), b, x0, tol, interior=ref.interior)
+        assert abs(itg - ito) <= 1
+        assert rel(host(xg), xo) <= 1e-10
+
+
+def test_pcg_async_edge_cases(sg):
+    ref, rng, xs = _problem((2, 3, 2), 3, 1.0, seed=51)
+    op = sg.Op(2, 3, 2, 3, 1.0, "f64")
+    b = dev(ref.apply(xs))
+    x = dev(xs)                                   # exact guess: 0 iterations
+    op.pcg_async(b, x, 1e-10)
+    assert op.pcg_result() == 0
+    x = op.zeros()                                # b = 0
+    op.pcg_async(op.zeros(), x, 1e-10)
+    assert op.pcg_result() == 0 and float(x.abs().max()) == 0.0
+    x = op.zeros()                                # maxit
+    op.pcg_async(b, x, 1e-14, maxit=3)
+    assert op.pcg_result() == 3
+    with pytest.raises(sg.SGError):
+        op.pcg_async(b, op.zeros(), 1e-14, maxit=3)
+        op.pcg_result(raise_on_maxit=True)
+    bn = ref.apply(xs)                            # NaN right-hand side
+    bn[np.flatnonzero(ref.interior)[3]] = np.nan
+    op.pcg_async(dev(bn), op.zeros(), 1e-10)
+    with pytest.raises(sg.SGError) as ei:
+        op.pcg_result()
+    assert ei.value.code == sg.ERR_BREAKDOWN
+    x = op.zeros()                                # a normal solve afterwards
+    op.pcg_async(b, x, 1e-10)
+    assert op.pcg_result() > 0
+    assert op.residual_norm(b, x) <= 1e-10
+
+
+def test_pcg_graph_cache_over_many_workspaces(sg):
+    """More workspaces than the per-operator graph cache holds (8): every solve
+    is right, and re-used workspaces hit the cache."""
+    import ctypes
+    ref, b, x0 = _pcg_problem(seed=52)
+    op = sg.Op(4, 3, 3, 5, 20.0, "f64")
+    nb = int(sg.lib().sg_pcg_workspace_bytes(op.h))
+    wss = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(11)]
+    bd = dev(b)
+    ref_x, ref_it = None, None
+    for rnd in range(2):
+        for ws in wss:
+            x = dev(x0)
+            it = ctypes.c_int(0)
+            rc = sg.lib().sg_pcg_solve(op.h, ctypes.c_void_p(bd.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                       1e-10, 10000, 0, ctypes.c_void_p(ws.data_ptr()), ctypes.byref(it), None,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+            assert rc == 0
+            if ref_x is None:
+                ref_x, ref_it = x.clone(), it.value
+            assert it.value == ref_it and torch.equal(x, ref_x)
