@@ -26,7 +26,9 @@
 //   z: each thread contracts its own column in registers; the top output of a
 //      layer is carried to the next layer's bottom node;
 //   x: item (plane c, row y, element) -> p outputs written to a work buffer;
-//   y: item (plane c, column x, element) -> p outputs written to the buffer;
+//   y: item (plane c, column x, element) -> p outputs; FP64 adds them to the
+//      x results in the same buffer (three barriers per layer), FP32 writes a
+//      second buffer (two barriers);
 // the thread then adds its column's x and y results, the mass term and the
 // weights, and stores.  The upper Dirichlet faces (index n-1) are written 0.
 //
@@ -315,12 +317,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
 #pragma unroll
       for (int c = 0; c < P; ++c) w[c] = o[c];
     }
-    if constexpr (!TWO_W) {
-      __syncthreads();
-#pragma unroll
-      for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
-      __syncthreads();
-    }
+    if constexpr (!TWO_W) __syncthreads();      // x results visible to the y items
 
     // epilogue operands of this layer's owned nodes, loaded before the y
     // contraction to overlap their latency with it
@@ -346,8 +343,13 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       dir_line<T, P, CREG>(ue, o, sTab[1], rt, sy);
       o[0] += dir_row<T, P, CREG>(ul, sTab[1], rt, sy);
       T* w = Wy + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
+      if constexpr (TWO_W) {
 #pragma unroll
-      for (int c = 0; c < P; ++c) w[(size_t)c * TX] = o[c];
+        for (int c = 0; c < P; ++c) w[(size_t)c * TX] = o[c];
+      } else {                                   // one buffer: add to the node's x result
+#pragma unroll
+        for (int c = 0; c < P; ++c) w[(size_t)c * TX] += o[c];
+      }
     }
     __syncthreads();
     if constexpr (TWO_W) {
