@@ -51,6 +51,8 @@ struct BatchArgs {
   unsigned int* bar;        // [0] arrivals, [1] generation
   int* err;
   int nblocks;
+  cudaGraphConditionalHandle cond;   // WHILE condition of the iteration graph (use_cond)
+  int use_cond;
 };
 
 // Grid-wide barrier for a cooperative launch, bounded spin (error flag on expiry).
@@ -101,10 +103,15 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
       }
       all &= s_done[s];
     }
-    s_all_done = all;
+    // an expired barrier wait in an earlier launch stops the iterations (the
+    // flag was written before this launch began, so every CTA reads the same)
+    s_all_done = all || *(volatile int*)A.err;
   }
   __syncthreads();
-  if (s_all_done) return;   // uniform over the grid: no barrier is entered
+  if (s_all_done) {         // uniform over the grid: no barrier is entered
+    if (A.use_cond && blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(A.cond, 0u);
+    return;
+  }
 
   // ---- phase A: operator items
   float pq[NS];
@@ -225,6 +232,12 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
           if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
         }
       }
+      if (A.use_cond) {       // continue while a system runs and no barrier wait expired
+        int more = 0;
+        for (int s = 0; s < A.nseq; ++s) more |= !A.seq[s].st->done;
+        if (*(volatile int*)A.err) more = 0;
+        cudaGraphSetConditional(A.cond, more ? 1u : 0u);
+      }
     }
   }
 }
@@ -343,6 +356,7 @@ struct sg_batch_s {
   int graph_iters;
   cudaGraphExec_t graph;
   int graph_ready;
+  int graph_while;          // 1: the graph is one WHILE node (one launch per solve)
   cudaStream_t graph_stream;
 };
 
@@ -431,8 +445,10 @@ int build_items(sg_batch_t b, int zl, cudaStream_t s) {
   return SG_OK;
 }
 
-int launch_iter(sg_batch_t b, cudaStream_t s) {
+int launch_iter(sg_batch_t b, cudaStream_t s, cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
   BatchArgs A = make_args(b);
+  A.cond = cond;
+  A.use_cond = use_cond;
   void* params[] = {&A};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->nblocks);
@@ -497,6 +513,7 @@ extern "C" int sg_batch_create(sg_batch_t* out, int nseq, const sg_op_t* ops64, 
   b->max_items = L.max_items; b->max_blocks = L.max_blocks;
   b->graph_iters = 8;
   b->graph_ready = 0;
+  b->graph_while = 0;
   int per_sm = 0;
   int rc = max_coresident(&per_sm);
   if (rc) { delete b; return rc; }
@@ -535,23 +552,57 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
   k_batch_init<<<dim3(gx, b->nseq), 256, 0, s>>>(A, tol, maxit, reinterpret_cast<unsigned int*>(b->ws + b->off_counters),
                                                  reinterpret_cast<const int*>(b->ws + b->off_active));
   SG_LAUNCH_CHECK("k_batch_init");
-  // graph of graph_iters persistent iterations, captured once per stream
+  // The iterations as a CUDA graph, built once per stream: preferably a
+  // conditional WHILE node around one persistent launch (CTA 0 of every
+  // iteration sets the condition; one graph launch runs the whole solve),
+  // else graph_iters launches replayed until every system is done.
   if (!b->graph_ready || b->graph_stream != s) {
     if (b->graph_ready) { cudaGraphExecDestroy(b->graph); b->graph_ready = 0; }
     cudaStream_t cs;
     SG_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaGraph_t graph = nullptr;
+    int rc = SG_OK;
+    // WHILE form
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
-      for (int i = 0; i < b->graph_iters; ++i) {
-        int rc = launch_iter(b, cs);
-        if (rc) { cudaStreamEndCapture(cs, &graph); cudaStreamDestroy(cs); return rc; }
-      }
-      e = cudaStreamEndCapture(cs, &graph);
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
     }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      e = cudaGraphInstantiate(&b->graph, graph, 0);
-      cudaGraphDestroy(graph);
+      rc = launch_iter(b, cs, cond, 1);
+      cudaGraph_t body = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && rc == SG_OK) e = cudaGraphInstantiate(&b->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    b->graph_while = (e == cudaSuccess && rc == SG_OK);
+    if (!b->graph_while) {
+      // replay form
+      cudaGetLastError();
+      graph = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int i = 0; i < b->graph_iters; ++i) {
+          rc = launch_iter(b, cs);
+          if (rc) { cudaStreamEndCapture(cs, &graph); if (graph) cudaGraphDestroy(graph); cudaStreamDestroy(cs); return rc; }
+        }
+        e = cudaStreamEndCapture(cs, &graph);
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+      }
     }
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
@@ -560,7 +611,7 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
   }
   PollS poll[SG_BATCH_MAX];
   int done_all = 0, replays = 0;
-  const int max_replays = maxit / b->graph_iters + 2;
+  const int max_replays = b->graph_while ? 1 : maxit / b->graph_iters + 2;
   while (!done_all) {
     SG_CUDA_TRY(cudaGraphLaunch(b->graph, s));
     ++replays;
@@ -572,7 +623,12 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
     if (err) return sg_fail(SG_ERR_TIMEOUT, "batch: grid barrier wait expired");
     done_all = 1;
     for (int k = 0; k < b->nseq; ++k) done_all &= poll[k].done;
-    if (replays > max_replays) break;
+    if (b->graph_while) {        // persistent launches the WHILE node ran
+      int most = 1;
+      for (int k = 0; k < b->nseq; ++k) if (active[k] && poll[k].iter > most) most = poll[k].iter;
+      sg_count_launches(most);
+    }
+    if (replays >= max_replays) break;
   }
   for (int k = 0; k < b->nseq; ++k) {
     if (iters) iters[k] = active[k] ? poll[k].iter : 0;

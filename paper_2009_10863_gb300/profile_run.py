@@ -2,9 +2,15 @@
 mesh of the bench's shapes, for profiling (ncu) and quick timing.
 
     python -m paper_2009_10863_gb300.profile_run --elements 16 --dtype f64
+    python -m paper_2009_10863_gb300.profile_run --steps 6
 
-It applies the operator `--reps` times (timed with CUDA events), runs a few
-PCG iterations, forms an EXTRAP(2,8) guess and performs QR(8) history updates.
+The first form applies the operator `--reps` times (timed with CUDA events),
+runs a few PCG iterations, forms an EXTRAP(2,8) guess and performs QR(8)
+history updates.  The second runs time steps of the bench's headline sequence
+(FP64 16^3 p = 7 Helmholtz, EXTRAP(2,8), 1e-10) with every library launch timed
+by CUDA events, so that the PCG iterations are host launches that a
+profiler lists one by one (the bench's timed steps run them inside CUDA-graph
+WHILE loops) -- the workload of the committed launch list.
 """
 import argparse
 
@@ -23,9 +29,12 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--pcg-iters", type=int, default=6)
     ap.add_argument("--s", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=0)
     args = ap.parse_args()
     from paper_2009_10863_gb300 import build
     build.build()
+    if args.steps > 0:
+        return headline_steps(args.steps)
     E = args.elements
     op = sg.Op(E, E, E, args.p, args.lam, args.dtype)
     gen = torch.Generator(device="cuda").manual_seed(0)
@@ -54,6 +63,32 @@ def main():
     torch.cuda.synchronize()
     print("nodes %d dtype %s apply %.1f us, pcg iterations %d, qr d=%d" %
           (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, q.info()[0]))
+
+
+def headline_steps(steps):
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from bench import Workload, CFG
+    wl = Workload(sg, torch, steps, torch.device("cuda", 0))
+    op = wl.op
+    g = sg.Guess(op.n, CFG["s"], "extrap", m=2, eps_rel=CFG["tol"], op=op)
+    sg.profile_reset()
+    sg.profile_enable(True)
+    iters = []
+    for k in range(steps):
+        x = g.next_slot()
+        g.form(wl.rhs[k], x)
+        it, _ = op.pcg(wl.rhs[k], x, CFG["tol"], true_residual=False)
+        g.update(x)
+        iters.append(it)
+    torch.cuda.synchronize()
+    sg.profile_enable(False)
+    for name, kid in (("pcg_apply", sg.PROF_PCG_APPLY), ("pcg_update", sg.PROF_PCG_UPDATE),
+                      ("extrap", sg.PROF_EXTRAP)):
+        t, c = sg.profile_read(kid)
+        print("%-10s %5d launches %9.1f us" % (name, c, 1e3 * t))
+    print("iterations per step", iters)
 
 
 if __name__ == "__main__":
