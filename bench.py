@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
-PCG_APPLY_TRAFFIC = 33920256 + 0
+PCG_APPLY_TRAFFIC = 33918848 + 0  # mean of the two not-first MODE 1 launches
 
 
 def aggregate_max(value, dist, device):
@@ -169,8 +169,9 @@ MIXED_PROF_STEPS = 2
 
 
 def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
-    """C3-style steps: mode 'ir' = FP32 history + FP32 PCG in FP64 refinement,
-    mode 'f64' = FP64 history + FP64 PCG.  Returns per-step ms and iterations.
+    """C3-style steps: mode 'ir' = FP32 history + FP32 PCG in restarted FP64
+    refinement, 'ru' = the same with FP64 residual replacement instead of
+    restarts, 'f64' = FP64 history + FP64 PCG.  Returns per-step ms and iterations.
     The timed steps run the solves as in production (iterations in graph
     launches); MIXED_PROF_STEPS further steps, untimed, time every kernel
     launch with CUDA events for the per-kernel breakdown."""
@@ -179,7 +180,7 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
     n = wl.op.n
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     its, outs, rels = [], [], []
-    if mode == "ir":
+    if mode in ("ir", "ru"):
         ms = sg.MixedSolver(*c["E"], c["p"], c["lam"])
         g = sg.Guess(n, s, "extrap", m=m, dtype="f32")
         x64 = ms.op64.zeros()
@@ -197,9 +198,9 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
         b = wl.rhs[k]
         slot = g.next_slot()
         g.form(None, slot)
-        if mode == "ir":
+        if mode in ("ir", "ru"):
             sg.convert(slot, x64)
-            o, i, r = ms.solve(b, x64, tol)
+            o, i, r = ms.solve(b, x64, tol, method="restart" if mode == "ir" else "replace")
             sg.convert(x64, slot)
             if timed:
                 outs.append(o)
@@ -209,7 +210,7 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
         if timed:
             ev[k - warmup][1].record()
             its.append(i)
-            rels.append(r if mode == "ir" else op.residual_norm(b, slot))   # FP64 check, untimed
+            rels.append(r if mode in ("ir", "ru") else op.residual_norm(b, slot))   # FP64 check, untimed
         flush()
     torch.cuda.synchronize()
     sg.profile_enable(False)
@@ -581,6 +582,7 @@ def main():
         torch.cuda.empty_cache()
         w3 = Workload(sg, torch, args.mixed_warmup + args.mixed_steps + MIXED_PROF_STEPS, device, cfg=c3)
         r_ir = run_mixed(sg, torch, w3, c3["s"], 2, args.mixed_steps, args.mixed_warmup, flush, "ir")
+        r_ru = run_mixed(sg, torch, w3, c3["s"], 2, args.mixed_steps, args.mixed_warmup, flush, "ru")
         r_64 = run_mixed(sg, torch, w3, c3["s"], 2, args.mixed_steps, args.mixed_warmup, flush, "f64")
         n3 = w3.op.n
         ex32_gbs = (c3["s"] + 1) * 4 * n3 / (r_ir["extrap_avg_ms"] * 1e-3) / 1e9
@@ -590,9 +592,13 @@ def main():
             "fp32_ir": {"ms_per_step": r_ir["ms"], "inner_fp32_iters_per_step": r_ir["iters"],
                         "outer_steps_per_step": r_ir["outer"], "max_relres_fp64": r_ir["max_relres"],
                         "kernels": r_ir["kernels"]},
+            "fp32_replace": {"ms_per_step": r_ru["ms"], "inner_fp32_iters_per_step": r_ru["iters"],
+                             "fp64_updates_per_step": r_ru["outer"], "max_relres_fp64": r_ru["max_relres"],
+                             "kernels": r_ru["kernels"]},
             "fp64": {"ms_per_step": r_64["ms"], "cg_iters_per_step": r_64["iters"],
                      "max_relres": r_64["max_relres"], "kernels": r_64["kernels"]},
             "speedup_fp32_ir_vs_fp64": r_64["ms"] / r_ir["ms"],
+            "speedup_fp32_replace_vs_fp64": r_64["ms"] / r_ru["ms"],
             "extrap_fp32": {"GB_s": ex32_gbs, "frac_of_hbm": ex32_gbs / hbm_gbs,
                             "bytes_per_launch": (c3["s"] + 1) * 4 * n3}}
         del w3

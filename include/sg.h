@@ -173,6 +173,21 @@ int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, 
                 int max_outer, int maxit_inner, void* workspace, int* outer_iters, int* inner_iters,
                 double* relres, void* stream);
 
+/* The same problem by one FP32 Jacobi-PCG whose residual is replaced by the
+ * FP64 residual at reliable updates (residual replacement, van der Vorst & Ye
+ * 2000; no counterpart in the paper, whose solver runs in FP64): whenever the
+ * FP32 residual has dropped by t = min(0.1, max(delta, tol ||b|| / (2 ||r||)))
+ * since the last update, x += x32 in FP64, r = b - A64 x, the FP32 residual
+ * and preconditioned residual are reset from r and CG continues with its
+ * search direction (beta from the replaced residual) instead of restarting.
+ * Same operators, vectors, workspace (sg_ir_workspace_bytes) and errors as
+ * sg_ir_solve.  max_updates bounds the FP64 updates, maxit_inner the FP32
+ * iterations in total.  updates, inner_iters, relres: HOST outputs, may be
+ * NULL.  Synchronises with ``stream`` once per update. */
+int sg_ir_solve_ru(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double delta,
+                   int max_updates, int maxit_inner, void* workspace, int* updates, int* inner_iters,
+                   double* relres, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched sequences.  The paper keeps one history space per velocity
  * component and one for the pressure (Sec. 6.1) and solves each system by

@@ -60,6 +60,8 @@ SIGNATURES = [
     ("sg_ir_workspace_bytes", _SZ, [_VP, _VP]),
     ("sg_ir_solve", _I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_D), _VP]),
+    ("sg_ir_solve_ru", _I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, _VP, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), _VP]),
     ("sg_batch_workspace_bytes", _SZ, [_I, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     ("sg_batch_create", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("sg_batch_destroy", _I, [_VP]),
@@ -318,14 +320,26 @@ class MixedSolver:
         nb = int(lib().sg_ir_workspace_bytes(self.op64.h, self.op32.h))
         self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
 
-    def solve(self, b, x, tol, inner_tol=1e-4, max_outer=30, maxit_inner=10000):
-        """Solve in place; returns (outer steps, total inner FP32 iterations, FP64 relres)."""
+    def solve(self, b, x, tol, inner_tol=None, max_outer=30, maxit_inner=10000, method="restart"):
+        """Solve in place; returns (outer steps or FP64 updates, total inner FP32
+        iterations, FP64 relres).  method "restart": refinement with an FP32 PCG
+        solve from zero per outer step to inner_tol (default 1e-4; sg_ir_solve);
+        "replace": one FP32 PCG with its residual replaced by the FP64 one each
+        time it has dropped by inner_tol (default 0.1; sg_ir_solve_ru)."""
+        if inner_tol is None:
+            inner_tol = 1e-4 if method == "restart" else 0.1
         self.op64._vec(b, "b")
         self.op64._vec(x, "x")
         oi, ii, rr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
-        _check(lib().sg_ir_solve(self.op64.h, self.op32.h, _ptr(b), _ptr(x), float(tol), float(inner_tol),
-                                 int(max_outer), int(maxit_inner), _ptr(self.ws), ctypes.byref(oi),
-                                 ctypes.byref(ii), ctypes.byref(rr), _stream()), (OK, NOT_CONVERGED))
+        if method == "restart":
+            fn = lib().sg_ir_solve
+        elif method == "replace":
+            fn = lib().sg_ir_solve_ru
+        else:
+            raise ValueError("method must be 'restart' or 'replace'")
+        _check(fn(self.op64.h, self.op32.h, _ptr(b), _ptr(x), float(tol), float(inner_tol), int(max_outer),
+                  int(maxit_inner), _ptr(self.ws), ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr),
+                  _stream()), (OK, NOT_CONVERGED))
         return oi.value, ii.value, rr.value
 
 

@@ -759,3 +759,155 @@ extern "C" int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, d
   }
   return SG_OK;
 }
+
+// ---------------------------------------------------------------- FP32 PCG with FP64 residual replacement
+// Restarted refinement (sg_ir_solve) begins every inner solve from d = 0 and
+// loses its Krylov space; FP32 CG then needs about twice the FP64 iteration
+// count.  Here one FP32 PCG runs across the whole solve and its residual is
+// replaced by the FP64 one at "reliable updates" (residual replacement: van der
+// Vorst & Ye, SIAM J. Sci. Comput. 22 (2000); the mixed-precision form of
+// Clark et al., Comput. Phys. Commun. 181 (2010)): whenever the FP32
+// recursive residual has dropped by delta since the last update,
+//   x64 += x32, x32 = 0;  r64 = b - A64 x64;  r32 = (float) r64;
+//   z = r32 / diag(A);  beta = (r32.z) / (r.z)_previous;  p, q kept,
+// so the next operator step forms p = z + beta p, q = A z + beta q and CG
+// continues with its search direction.  The solution is accumulated and the
+// stopping test taken in FP64.
+
+// Start of a segment after an FP64 update: r32 = (float) r64, z = r32 / diag,
+// r.r and r.z; the last block continues the PCG state (first = 0) with the
+// new residual and sets the segment's threshold (seg_tol relative to it).
+// When the true residual is more than twice the FP32 recursive one it ended
+// the segment with, the two have drifted apart and the kept direction no
+// longer fits: the search direction restarts (first = 1, p = z).
+__global__ void __launch_bounds__(256) k_ru_restart(const double* __restrict__ r64, float* __restrict__ r32,
+                                                   const float* __restrict__ invd, float* __restrict__ z, int n,
+                                                   double seg_tol, PcgState* st, double* partials) {
+  __shared__ double sred[64];
+  double rr = 0.0, rz = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float rv = (float)r64[i];
+    const float zv = rv * invd[i];
+    r32[i] = rv;
+    z[i] = zv;
+    rr += (double)rv * rv;
+    rz += (double)rv * zv;
+  }
+  double v[2] = {rr, rz}, tot[2];
+  if (grid_reduce_last<2>(v, partials, &st->counter[1], sred, tot)) {
+    if (threadIdx.x == 0) {
+      const double rz_old = st->rz;
+      const double rr_rec = st->rr;
+      st->rr = tot[0];
+      st->thr2 = seg_tol * seg_tol * tot[0];
+      st->first = (tot[0] > 4.0 * rr_rec) ? 1 : 0;
+      st->done = 0;
+      st->status = PCG_RUNNING;
+      if (!isfinite(tot[0]) || !isfinite(tot[1]) || !(rz_old > 0.0)) { st->status = PCG_BREAKDOWN; st->done = 1; }
+      else {
+        st->beta = st->first ? 0.0 : tot[1] / rz_old;
+        st->rz = tot[1];
+        if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
+      }
+    }
+  }
+}
+
+__global__ void k_add_correction_reset(double* __restrict__ x, float* __restrict__ d, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] += (double)d[i];
+    d[i] = 0.f;
+  }
+}
+
+extern "C" int sg_ir_solve_ru(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double delta,
+                              int max_updates, int maxit_inner, void* workspace, int* updates, int* inner_iters,
+                              double* relres, void* stream) {
+  if (!op64 || !op32 || !b || !x || !workspace) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: NULL argument");
+  if (op64->dtype != SG_F64 || op32->dtype != SG_F32)
+    return sg_fail(SG_ERR_INVALID, "ir_solve_ru: needs an FP64 and an FP32 operator");
+  if (!same_geometry(op64, op32)) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: operators differ in mesh or lambda");
+  if (!(tol > 0.0) || !(delta > 0.0) || !(delta < 1.0)) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: need tol > 0, 0 < delta < 1");
+  if (max_updates < 0 || maxit_inner < 0) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: iteration limits must be >= 0");
+  if (!aligned16(b) || !aligned16(x)) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: vectors must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return sg_fail(SG_ERR_INVALID, "ir_solve_ru: workspace must be 256-byte aligned");
+  const IrLayout I = ir_layout(op64, op32);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  unsigned char* ws32 = ws + I.ws32;
+  PcgState* st64 = reinterpret_cast<PcgState*>(ws + I.state);
+  PcgState* st32 = reinterpret_cast<PcgState*>(ws32 + I.L32.state);
+  double* partials = reinterpret_cast<double*>(ws + I.partials);
+  double* r64 = reinterpret_cast<double*>(ws + I.r64);
+  float* r32 = reinterpret_cast<float*>(ws + I.r32);
+  float* d32 = reinterpret_cast<float*>(ws + I.d32);
+  const double* b64 = static_cast<const double*>(b);
+  double* x64 = static_cast<double*>(x);
+  const int n = (int)op64->n;
+  const int nb = flat_blocks(n);
+  cudaStream_t s = as_stream(stream);
+  auto fp64_residual = [&]() -> int {     // r64 = b - A64 x64, ||r64||^2 and ||b||^2 into st64
+    k_pcg_setup<<<1, 32, 0, s>>>(st64, tol, 0, SG_STOP_REL_B, nullptr);
+    SG_LAUNCH_CHECK("k_pcg_setup");
+    SemArgs<double> a{};
+    a.x = x64; a.aux = b64; a.out = r64; a.partials = partials; a.st = st64; a.final_pass = 1;
+    return sg_sem_launch<double, 2>(op64->g, a, s, 0);
+  };
+  k_mask_faces<double><<<64, 256, 0, s>>>(x64, op64->g.nx, op64->g.ny, op64->g.nz);
+  SG_LAUNCH_CHECK("k_mask_faces");
+  int rc = fp64_residual();
+  if (rc) return rc;
+  PcgState h64, h32;
+  SG_CUDA_TRY(cudaMemcpyAsync(&h64, st64, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  const double bb = h64.bb;
+  double rel = bb > 0 ? sqrt(h64.rr_true / bb) : sqrt(h64.rr_true);
+  if (!std::isfinite(rel)) return sg_fail(SG_ERR_BREAKDOWN, "ir_solve_ru: non-finite residual");
+  int nupd = 0, inner = 0;
+  bool started = false;
+  cudaGraphExec_t exec = nullptr;
+  while (rel > tol && nupd < max_updates) {
+    const double seg_tol = ir_inner_tol(delta, tol, rel);
+    if (!started) {                 // first segment: PCG from x32 = 0 on r32 = (float) r64
+      k_convert<double, float><<<nb, 256, 0, s>>>(r64, r32, n);
+      SG_LAUNCH_CHECK("k_convert");
+      SG_CUDA_TRY(cudaMemsetAsync(d32, 0, sizeof(float) * (size_t)n, s));
+      rc = pcg_start<float>(op32, r32, d32, seg_tol, maxit_inner, SG_STOP_REL_B, ws32, I.L32, s);
+      if (rc) return rc;
+      started = true;
+    } else {                        // later segments: residual replaced, search direction kept
+      k_ru_restart<<<update_blocks(op32->n, 4), 256, 0, s>>>(r64, reinterpret_cast<float*>(ws32 + I.L32.r),
+                                                            reinterpret_cast<const float*>(ws32 + I.L32.invd),
+                                                            reinterpret_cast<float*>(ws32 + I.L32.z), n, seg_tol, st32,
+                                                            reinterpret_cast<double*>(ws32 + I.L32.partials));
+      SG_LAUNCH_CHECK("k_ru_restart");
+    }
+    if (!exec) exec = iteration_graph<float>(op32, ws32, I.L32);
+    if (exec) {
+      SG_CUDA_TRY(cudaGraphLaunch(exec, s));
+    } else {
+      rc = pcg_iterate_launches<float, false>(op32, d32, maxit_inner, ws32, I.L32, s);
+      if (rc) return rc;
+    }
+    k_add_correction_reset<<<nb, 256, 0, s>>>(x64, d32, n);
+    SG_LAUNCH_CHECK("k_add_correction_reset");
+    rc = fp64_residual();
+    if (rc) return rc;
+    ++nupd;
+    SG_CUDA_TRY(cudaMemcpyAsync(&h32, st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(&h64, st64, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (exec) sg_count_launches(2 * (h32.iter - inner > 0 ? h32.iter - inner : 1));
+    inner = h32.iter;
+    rel = bb > 0 ? sqrt(h64.rr_true / bb) : sqrt(h64.rr_true);
+    if (!std::isfinite(rel) || h32.status == PCG_BREAKDOWN) return sg_fail(SG_ERR_BREAKDOWN, "ir_solve_ru: breakdown");
+    if (h32.status == PCG_MAXIT) break;
+  }
+  if (updates) *updates = nupd;
+  if (inner_iters) *inner_iters = inner;
+  if (relres) *relres = rel;
+  if (rel > tol) {
+    sg_set_error("ir_solve_ru: update or inner iteration limit reached");
+    return SG_NOT_CONVERGED;
+  }
+  return SG_OK;
+}

@@ -5,8 +5,8 @@ mesh of the bench's shapes, for profiling (ncu) and quick timing.
     python -m paper_2009_10863_gb300.profile_run --steps 6
 
 The first form applies the operator `--reps` times (timed with CUDA events),
-runs a few PCG iterations, forms an EXTRAP(2,8) guess and performs QR(8)
-history updates.  The second runs time steps of the bench's headline sequence
+runs a few PCG iterations (host-launched, as with kernel timing on), forms an
+EXTRAP(2,8) guess and performs QR(8) history updates.  The second runs time steps of the bench's headline sequence
 (FP64 16^3 p = 7 Helmholtz, EXTRAP(2,8), 1e-10) with every library launch timed
 by CUDA events, so that the PCG iterations are host launches that a
 profiler lists one by one (the bench's timed steps run them inside CUDA-graph
@@ -44,7 +44,9 @@ def main():
         op.apply(x, out=y)
     b = op.apply(x)
     xs = op.zeros()
+    sg.profile_enable(True)      # host-launched iterations: each kernel is a separate launch
     it, _ = op.pcg(b, xs, 1e-10, maxit=args.pcg_iters)
+    sg.profile_enable(False)
     g = sg.Guess(op.n, args.s, "extrap", m=2, dtype=args.dtype)
     q = sg.Guess(op.n, args.s, "qr", eps_rel=1e-6, op=op, dtype=args.dtype)
     for k in range(args.s + 1):          # independent vectors: the QR history fills to d = s

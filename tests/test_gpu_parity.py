@@ -365,22 +365,63 @@ def test_c1_sequence_end_to_end(sg, method, mcode):
 
 
 # ---------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("method", ["restart", "replace"])
 @pytest.mark.parametrize("E,p,lam", [((4, 4, 4), 3, 0.0), ((3, 4, 5), 5, 50.0), ((4, 4, 3), 7, 0.0)])
-def test_fp32_ir_reaches_fp64_tolerance(sg, E, p, lam):
-    """FP32 operator/PCG wrapped in FP64 refinement meets ||b - A x|| <= 1e-10 ||b||
-    measured with the FP64 oracle operator; error vs the FP64 oracle solution is
-    reported and bounded."""
+def test_fp32_ir_reaches_fp64_tolerance(sg, E, p, lam, method):
+    """FP32 operator/PCG wrapped in FP64 refinement (restarted, or with residual
+    replacement) meets ||b - A x|| <= 1e-10 ||b|| measured with the FP64 oracle
+    operator; error vs the FP64 oracle solution is reported and bounded."""
     ref, rng, xs = _problem(E, p, lam, seed=8)
     b = ref.apply(xs)
     ms = sg.MixedSolver(*E, p, lam)
     x = ms.op64.zeros()
-    outer, inner, relg = ms.solve(dev(b), x, 1e-10, inner_tol=1e-5)
+    outer, inner, relg = ms.solve(dev(b), x, 1e-10, inner_tol=1e-5, method=method)
     xg = host(x)
     rel_oracle = np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b)
     assert relg <= 1e-10 and rel_oracle <= 1.01e-10
     assert outer >= 2 and inner > 0
     xo, _, _, _ = opcg(ref.apply, ref.diagonal(), b, np.zeros(ref.n), 1e-13, interior=ref.interior)
     assert rel(xg, xo) <= 1e-7
+
+
+def test_residual_replacement_keeps_the_krylov_space(sg):
+    """On a 12^3 p = 7 Poisson problem, FP32 PCG with FP64 residual replacement
+    (updates every 10x residual drop) needs fewer FP32 iterations than restarted
+    refinement (inner 1e-4); both reach 1e-10 in FP64, and neither is below the
+    FP64 PCG iteration count."""
+    E, p = (12, 12, 12), 7
+    op = sg.Op(*E, p, 0.0, "f64")
+    cx, cy, cz = op.coords_1d()
+    f = Modes(3, 8, 4).field(cx, cy, cz, 0.3)
+    b = op.apply(dev(f))
+    ms = sg.MixedSolver(*E, p, 0.0)
+    it64, _ = op.pcg(b, op.zeros(), 1e-10)
+    res = {}
+    for method in ("restart", "replace"):
+        x = ms.op64.zeros()
+        o, inner, relg = ms.solve(b, x, 1e-10, method=method)
+        assert relg <= 1e-10
+        assert op.residual_norm(b, x) <= 1e-10
+        res[method] = inner
+    assert res["replace"] < res["restart"]
+    assert min(res.values()) >= 0.9 * it64
+
+
+def test_residual_replacement_edge_cases(sg):
+    ref, rng, xs = _problem((3, 3, 3), 4, 2.0, seed=9)
+    ms = sg.MixedSolver(3, 3, 3, 4, 2.0)
+    b = dev(ref.apply(xs))
+    x = dev(xs)                                   # exact guess: no update
+    o, inner, relg = ms.solve(b, x, 1e-10, method="replace")
+    assert o == 0 and inner == 0 and relg <= 1e-10
+    x = ms.op64.zeros()                           # b = 0
+    o, inner, relg = ms.solve(ms.op64.zeros(), x, 1e-10, method="replace")
+    assert o == 0 and float(x.abs().max()) == 0.0
+    x = ms.op64.zeros()                           # update limit -> NOT_CONVERGED, best iterate kept
+    o, inner, relg = ms.solve(b, x, 1e-10, inner_tol=0.5, max_outer=1, method="replace")
+    assert o == 1 and relg > 1e-10
+    with pytest.raises(ValueError):
+        ms.solve(b, x, 1e-10, method="nope")
 
 
 def test_convert_roundtrip(sg):
