@@ -110,9 +110,11 @@ __global__ void __launch_bounds__(256) k_extrap(T* out, const ExtrapArgs<T> a, i
     V v[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = reinterpret_cast<const V*>(a.src[j])[i];   // all loads in flight
-    V acc = vzero<V>();
+    V acc;
 #pragma unroll
-    for (int j = 0; j < K; ++j)
+    for (int w = 0; w < W; ++w) vel(acc, w) = b[0] * vel(v[0], w);
+#pragma unroll
+    for (int j = 1; j < K; ++j)
 #pragma unroll
       for (int w = 0; w < W; ++w) vel(acc, w) += b[j] * vel(v[j], w);
     reinterpret_cast<V*>(out)[i] = acc;
@@ -592,7 +594,7 @@ int extrap_form(sg_guess_t g, void* x0, cudaStream_t s) {
   }
   a.k = nt;
   ProfScope ps(PROF_EXTRAP, s);
-  const int nb = reduce_blocks(g->n, VecT<T>::W) * 2;
+  const int nb = reduce_blocks(g->n, VecT<T>::W) * 2;   // up to 8 CTAs of 256 per SM (one wave)
   T* out = static_cast<T*>(x0);
   const int n = (int)g->n;
 #define SG_CALL(K) k_extrap<T, K><<<nb, 256, 0, s>>>(out, a, n)
