@@ -314,10 +314,15 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     iters, rels = [], []
     host_b = host_x = dev_b = None
+    # e2e: the extrapolation guess does not read b_k, so its host-to-device copy
+    # runs on a second stream while the guess is formed; the solve waits for it
+    overlap = e2e and method in ("extrap", "last", "zero", "spextrap")
     if e2e:
         host_b = [wl.rhs[k].cpu().pin_memory() for k in range(warmup + steps)]
         host_x = torch.empty(op.n, dtype=torch.float64).pin_memory()
         dev_b = op.empty()
+        copy_stream = torch.cuda.Stream()
+        copied = torch.cuda.Event()
     launches = 0
     if clocks:
         clocks.start()
@@ -334,7 +339,13 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
         if timed:
             ev[k - warmup][0].record()
         if e2e:
-            dev_b.copy_(host_b[k], non_blocking=True)
+            if overlap:
+                copy_stream.wait_stream(torch.cuda.current_stream())   # step k-1 done with dev_b
+                with torch.cuda.stream(copy_stream):
+                    dev_b.copy_(host_b[k], non_blocking=True)
+                copied.record(copy_stream)
+            else:
+                dev_b.copy_(host_b[k], non_blocking=True)
             b = dev_b
         else:
             b = wl.rhs[k]
@@ -342,6 +353,8 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
         if method == "zero":
             x.zero_()
         g.form(b, x)
+        if overlap:
+            torch.cuda.current_stream().wait_event(copied)
         if prof:
             it, _ = op.pcg(b, x, tol, true_residual=False)
         else:
