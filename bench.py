@@ -298,7 +298,8 @@ def run_batched(sg, torch, device, steps, warmup, flush, mode, tune=True):
             "tuned": {"zl": tuned[0], "ctas_per_sm": tuned[1], "ms_per_iter": tuned[2]} if tuned else None}
 
 
-def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, clocks=None, e2e=False):
+def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, clocks=None, e2e=False,
+               criterion=0):
     """Run warmup + steps time steps; returns per-step ms, iterations, residuals.
 
     Without ``prof`` every solve is enqueued with ``Op.pcg_async`` (set-up
@@ -356,9 +357,9 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
         if overlap:
             torch.cuda.current_stream().wait_event(copied)
         if prof:
-            it, _ = op.pcg(b, x, tol, true_residual=False)
+            it, _ = op.pcg(b, x, tol, criterion=criterion, true_residual=False)
         else:
-            op.pcg_async(b, x, tol)
+            op.pcg_async(b, x, tol, criterion=criterion)
         g.update(x)
         if e2e:
             host_x.copy_(x, non_blocking=True)
@@ -582,12 +583,29 @@ def main():
     # the other guess methods on the same sequence (not part of the headline)
     if not args.no_compare:
         comp = {}
-        for name, m in (("zero", 0), ("last", 0), ("qr", 0)):
+        # ZERO, LAST, QR(8) (Algorithm 2), and the rows beyond the paper's main
+        # comparison: naive extrapolation EXTRAP(7,8) (degree M-1, the paper's
+        # unstable baseline), SPEXTRAP(2,8), CLASSIC(8) (Algorithm 1)
+        for label, name, m in (("zero", "zero", 0), ("last", "last", 0), ("qr", "qr", 0),
+                               ("naive extrap(7,8)", "extrap", 7), ("spextrap(2,8)", "spextrap", 2),
+                               ("classic(8)", "classic", 0)):
             r = run_method(sg, torch, wl, name, m, s, args.steps, args.warmup, flush)
-            comp[name] = {"ms_per_step": sum(r["ms"]) / len(r["ms"]),
-                          "cg_iters_per_step": sum(r["iters"]) / len(r["iters"])}
+            comp[label] = {"ms_per_step": sum(r["ms"]) / len(r["ms"]),
+                           "cg_iters_per_step": sum(r["iters"]) / len(r["iters"]),
+                           "max_relres": max(r["rels"])}
         comp["extrap(2,8)"] = {"ms_per_step": ms_step, "cg_iters_per_step": out["cg_iters_per_step"]}
         out["methods"] = comp
+        # the paper's two stopping rules (Eqs. StopCritINITRESID, StopCritRHS) against
+        # the workload's ||r|| <= tol ||b||, same EXTRAP(2,8) sequence
+        crit = {}
+        for label, code in (("||r|| < tol max(||r0||, 1)", sg.STOP_INITRESID),
+                            ("||r|| < tol max(||b||, 1)", sg.STOP_RHS)):
+            r = run_method(sg, torch, wl, HEADLINE[0], HEADLINE[1], s, args.steps, args.warmup, flush,
+                           criterion=code)
+            crit[label] = {"ms_per_step": sum(r["ms"]) / len(r["ms"]),
+                           "cg_iters_per_step": sum(r["iters"]) / len(r["iters"]),
+                           "max_relres": max(r["rels"])}
+        out["stopping_rules"] = crit
 
     if not args.no_mixed:
         c3 = CONFIGS["c3"]

@@ -285,3 +285,26 @@ def test_table1_counts_golden():
     assert want["QR"] == (2 * (M + 1), 10 * M + 24, 12 * M + 26)
     assert want["EXTRAP"] == (M + 1, 0, M + 1)
     assert want["SPEXTRAP"] == (m + 2, 0, m + 2)
+
+
+def test_lebesgue_curves_golden_and_bounds():
+    """The committed Lebesgue-constant curves (written from the oracle by
+    tests/golden/make_lebesgue_curves.py) still follow from the oracle; every
+    weight vector reproduces constants (sum beta = 1, hence Lambda >= 1); naive
+    extrapolation has Lambda = 2^M - 1 and the degree-floor(sqrt(M)) fits stay
+    below it (Sec. 6.6)."""
+    rows = _golden_rows("lebesgue_curves.txt")
+    assert [int(r[0]) for r in rows] == list(range(1, 17))
+    for r in rows:
+        M, m = int(r[0]), int(r[1])
+        lam_naive, lam_lsq, lam_sp = float(r[2]), float(r[3]), float(r[4])
+        b_lsq, b_sp = ex.lsq_coeffs(M, m), ex.sparse_coeffs(M, m)
+        assert abs(ex.lebesgue_constant(b_lsq) - lam_lsq) <= 1e-12 * lam_lsq
+        assert abs(ex.lebesgue_constant(b_sp) - lam_sp) <= 1e-12 * lam_sp
+        assert lam_naive == 2.0 ** M - 1
+        for b in (b_lsq, b_sp):
+            assert abs(np.sum(b) - 1.0) <= 1e-12
+        assert lam_lsq >= 1.0 - 1e-12 and lam_sp >= 1.0 - 1e-12
+        assert lam_lsq <= lam_naive + 1e-9 and lam_sp <= lam_naive + 1e-9
+        if m < M - 1:
+            assert lam_lsq < lam_naive
