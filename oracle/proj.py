@@ -1,4 +1,5 @@
-"""Right-hand-side projection guesses (FP64, CPU): Algorithms 1 and 2.
+"""Right-hand-side projection guesses (FP64, CPU): Algorithms 1 and 2, and the
+same rolling window in the energy inner product (ProjectionEnergy).
 
 Sec. 2: with an orthonormal basis B~ of the stored right-hand sides and the
 matching solutions X~ (A X~ = B~), the guess for A x = b is x0 = X~ B~^T b,
@@ -139,5 +140,75 @@ class ProjectionClassic:
         if nb > self.eps_rel * nrm0:
             self.B.append(bt / nb)
             self.X.append(xt / nb)
+            return True
+        return False
+
+
+class ProjectionEnergy:
+    """Projection in the energy inner product (x, y)_A = x^T A y, history size M.
+
+    Fischer's form of the projection (Comput. Methods Appl. Mech. Engrg. 163,
+    1998) keeps X~ A-orthonormal (X~^T A X~ = I) with B~ = A X~; the guess
+    x0 = X~ X~^T b is the A-orthogonal projection of the solution A^{-1} b onto
+    span(X~), i.e. it minimises ||x - A^{-1} b||_A there (Sec. 2 states the
+    Euclidean ||b - A x||_2 form).  The history is the rolling window of
+    Algorithm 2 with every inner product taken in the A-inner product: CGS2
+    coefficients c = X~^T (A x) (= (x~_j, x)_A), the norm ||x~||_A =
+    sqrt(x~^T b~), the R factor X_window = X~ R, and the same Givens downdate
+    when d = M (a rotation of A-orthonormal columns stays A-orthonormal).
+    Reading of the acceptance test: keep the new direction when
+    ||x~ after CGS2||_A > eps_rel * ||x||_A.
+    """
+
+    def __init__(self, M, eps_rel, apply_A):
+        self.M, self.eps_rel, self.apply_A = int(M), float(eps_rel), apply_A
+        self.B, self.X = [], []
+        self.R = np.zeros((self.M + 1, self.M + 1))
+        self.accepted = []
+
+    @property
+    def d(self):
+        return len(self.X)
+
+    def form(self, b, x0):
+        """x0 = X~ X~^T b when d > 0, else the caller's x0."""
+        if self.d == 0:
+            return np.array(x0, dtype=np.float64, copy=True)
+        c = np.array([np.dot(Xi, b) for Xi in self.X])
+        x = np.zeros_like(np.asarray(b, dtype=np.float64))
+        for ci, Xi in zip(c, self.X):
+            x = x + ci * Xi
+        return x
+
+    _downdate = ProjectionQR._downdate
+
+    def update(self, x, b=None):
+        xt = np.array(x, dtype=np.float64, copy=True)
+        bt = self.apply_A(xt)
+        nrm0 = np.sqrt(max(float(np.dot(xt, bt)), 0.0))
+        if self.d == self.M:
+            self._downdate()
+        d = self.d
+        if d == 0:
+            if nrm0 > 0.0:
+                self.R[0, 0] = nrm0
+                self.B, self.X = [bt / nrm0], [xt / nrm0]
+                self.accepted = [np.array(x, dtype=np.float64)]
+            return True
+        rcol = np.zeros(d)
+        for _ in range(2):                    # CGS2 in the A-inner product
+            c = np.array([np.dot(Xi, bt) for Xi in self.X])
+            for ci, Bi, Xi in zip(c, self.B, self.X):
+                bt = bt - ci * Bi
+                xt = xt - ci * Xi
+            rcol += c
+        nn = float(np.dot(xt, bt))
+        nb = np.sqrt(nn) if nn > 0.0 else 0.0
+        if nb > self.eps_rel * nrm0:
+            self.R[:d, d] = rcol
+            self.R[d, d] = nb
+            self.B.append(bt / nb)
+            self.X.append(xt / nb)
+            self.accepted.append(np.array(x, dtype=np.float64))
             return True
         return False

@@ -2,15 +2,16 @@
 
 Sec. 5.2 / 6.2: one linear system per time step, each solved by PCG from an
 initial guess built out of the stored history.  Methods (Sec. 4, Table 1
-nomenclature): ZERO, LAST, EXTRAP(m, M), SPEXTRAP(m, M), QR(M), CLASSIC(M).
+nomenclature): ZERO, LAST, EXTRAP(m, M), SPEXTRAP(m, M), QR(M), CLASSIC(M), and
+ENERGY(M), the rolling window of QR(M) in the energy inner product.
 """
 import numpy as np
 
 from . import extrap as ex
 from .pcg import pcg, REL_B
-from .proj import ProjectionQR, ProjectionClassic
+from .proj import ProjectionQR, ProjectionClassic, ProjectionEnergy
 
-ZERO, LAST, EXTRAP, PROJ_QR, PROJ_CLASSIC, SPEXTRAP = 0, 1, 2, 3, 4, 5
+ZERO, LAST, EXTRAP, PROJ_QR, PROJ_CLASSIC, SPEXTRAP, PROJ_ENERGY = 0, 1, 2, 3, 4, 5, 6
 
 
 class ExtrapHistory:
@@ -69,6 +70,8 @@ def make_guesser(method, op, s, m=None, eps_rel=1e-10):
         return ProjectionQR(s, eps_rel, op.apply)
     if method == PROJ_CLASSIC:
         return ProjectionClassic(s, eps_rel, op.apply)
+    if method == PROJ_ENERGY:
+        return ProjectionEnergy(s, eps_rel, op.apply)
     raise ValueError("unknown method")
 
 

@@ -16,7 +16,7 @@ import pytest
 from numpy.polynomial import Polynomial as Poly
 
 from oracle import extrap as ex
-from oracle.proj import ProjectionQR, ProjectionClassic
+from oracle.proj import ProjectionQR, ProjectionClassic, ProjectionEnergy
 from oracle.sem import SemOperator
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -262,6 +262,79 @@ def test_projection_beats_extrapolation_same_window():
     rP = np.linalg.norm(b - op.apply(P.form(b, np.zeros(op.n))))
     rE = np.linalg.norm(b - op.apply(ex.extrap_guess(xs, ex.lsq_coeffs(M, m))))
     assert rP <= rE
+
+
+def _check_energy_invariants(P, op, tol=1e-11):
+    B = np.array(P.B).T
+    X = np.array(P.X).T
+    d = P.d
+    AX = np.array([op.apply(X[:, i]) for i in range(d)]).T
+    assert np.linalg.norm(X.T @ AX - np.eye(d)) <= tol            # A-orthonormal
+    assert np.linalg.norm(AX - B) <= tol * np.linalg.norm(B)
+    Xw = np.array(P.accepted).T
+    R = P.R[:d, :d]
+    assert np.allclose(np.tril(R, -1), 0)
+    assert np.all(np.abs(np.diag(R)) > 0)
+    assert np.linalg.norm(X @ R - Xw) <= tol * np.linalg.norm(Xw)  # X_window = X~ R
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_energy_projection_invariants_and_bruteforce(M):
+    """Energy-norm projection: X~ stays A-orthonormal through CGS2 and the
+    Givens downdate, and the guess equals the brute-force minimiser of
+    ||x - A^{-1} b||_A over the raw accepted window (normal equations of the
+    window in the A-inner product, solved densely)."""
+    op, rng = _small_problem(11)
+    m = op.interior
+    P = ProjectionEnergy(M, 1e-12, op.apply)
+    base = rng.standard_normal((3, op.n)) * m
+    for k in range(9):
+        x = (np.cos(0.3 * k) * base[0] + np.sin(0.2 * k) * base[1]
+             + 0.1 * k * base[2] + 1e-3 * rng.standard_normal(op.n) * m)
+        P.update(x)
+        assert P.d == min(k + 1, M)
+        _check_energy_invariants(P, op)
+        b = op.apply(rng.standard_normal(op.n) * m)
+        g = P.form(b, np.zeros(op.n))
+        Xw = np.array(P.accepted).T
+        AXw = np.array([op.apply(Xw[:, i]) for i in range(P.d)]).T
+        alpha = np.linalg.solve(Xw.T @ AXw, Xw.T @ b)
+        assert np.linalg.norm(g - Xw @ alpha) <= 1e-9 * np.linalg.norm(Xw @ alpha)
+
+
+def test_energy_projection_minimises_the_energy_error():
+    """Same window: the energy-norm guess has the smaller A-norm error, the
+    Euclidean (Algorithm 2) guess the smaller residual; a solution in the span
+    is reproduced and then rejected as dependent."""
+    from synthetic import Modes
+    op = SemOperator(3, 3, 3, 3, 0.0)
+    cx, cy, cz = op.coords_1d()
+    modes = Modes(2, 8, 4)
+    A = op.dense()
+    idx = np.flatnonzero(op.interior)
+    xs = [modes.field(cx, cy, cz, 0.01 * k) * op.interior for k in range(1, 6)]
+    E = ProjectionEnergy(5, 0.0, op.apply)
+    Q = ProjectionQR(5, 0.0, op.apply)
+    for x in xs:
+        E.update(x)
+        Q.update(x)
+    xt = modes.field(cx, cy, cz, 0.06) * op.interior
+    b = op.apply(xt)
+
+    def anorm(v):
+        return float(np.sqrt(v[idx] @ A[np.ix_(idx, idx)] @ v[idx]))
+    gE, gQ = E.form(b, np.zeros(op.n)), Q.form(b, np.zeros(op.n))
+    assert anorm(gE - xt) <= anorm(gQ - xt) * (1 + 1e-12)
+    assert np.linalg.norm(b - op.apply(gQ)) <= np.linalg.norm(b - op.apply(gE)) * (1 + 1e-12)
+    rng = np.random.default_rng(12)
+    ys = rng.standard_normal((3, op.n)) * op.interior
+    F = ProjectionEnergy(6, 1e-8, op.apply)
+    for y in ys:
+        assert F.update(y)
+    yin = 0.4 * ys[1] - 2.0 * ys[2]
+    assert np.linalg.norm(F.form(op.apply(yin), np.zeros(op.n)) - yin) <= 1e-12 * np.linalg.norm(yin)
+    assert not F.update(0.5 * ys[0] + 0.25 * ys[2])
+    assert F.d == 3
 
 
 def test_classic_restart_cycle():
