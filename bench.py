@@ -585,10 +585,11 @@ def main():
         comp = {}
         # ZERO, LAST, QR(8) (Algorithm 2), and the rows beyond the paper's main
         # comparison: naive extrapolation EXTRAP(7,8) (degree M-1, the paper's
-        # unstable baseline), SPEXTRAP(2,8), CLASSIC(8) (Algorithm 1)
+        # unstable baseline), SPEXTRAP(2,8), CLASSIC(8) (Algorithm 1), ENERGY(8)
+        # (the QR(8) window in the energy inner product)
         for label, name, m in (("zero", "zero", 0), ("last", "last", 0), ("qr", "qr", 0),
                                ("naive extrap(7,8)", "extrap", 7), ("spextrap(2,8)", "spextrap", 2),
-                               ("classic(8)", "classic", 0)):
+                               ("classic(8)", "classic", 0), ("energy(8)", "energy", 0)):
             r = run_method(sg, torch, wl, name, m, s, args.steps, args.warmup, flush)
             comp[label] = {"ms_per_step": sum(r["ms"]) / len(r["ms"]),
                            "cg_iters_per_step": sum(r["iters"]) / len(r["iters"]),

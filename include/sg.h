@@ -50,7 +50,15 @@ enum sg_method {
   SG_EXTRAP = 2,        /* EXTRAP(m, s): least squares, Eq. LSQRCoeffs       */
   SG_PROJ_QR = 3,       /* QR(s): rolling-QR projection, Algorithm 2         */
   SG_PROJ_CLASSIC = 4,  /* CLASSIC(s): restarted projection, Algorithm 1     */
-  SG_SPEXTRAP = 5       /* SPEXTRAP(m, s): sparse, Eq. CPQRCoeffs            */
+  SG_SPEXTRAP = 5,      /* SPEXTRAP(m, s): sparse, Eq. CPQRCoeffs            */
+  SG_PROJ_ENERGY = 6    /* ENERGY(s): the rolling window of QR(s) in the
+                           energy inner product -- X~ A-orthonormal, guess
+                           x0 = X~ X~^T b minimising ||x - A^{-1} b||_A over
+                           the span (Sec. 2's projection in Fischer's norm);
+                           CGS2 coefficients X~^T (A x), ||x~||_A, same
+                           Givens downdate, acceptance ||x~||_A > eps_rel
+                           ||x_k||_A.  No counterpart among the paper's
+                           Algorithms 1-2, which use the Euclidean form.   */
 };
 
 /* PCG stopping rules (Sec. 6.4). */

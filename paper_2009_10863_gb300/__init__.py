@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 
 F64, F32 = 0, 1
-ZERO, LAST, EXTRAP, PROJ_QR, PROJ_CLASSIC, SPEXTRAP = 0, 1, 2, 3, 4, 5
+ZERO, LAST, EXTRAP, PROJ_QR, PROJ_CLASSIC, SPEXTRAP, PROJ_ENERGY = 0, 1, 2, 3, 4, 5, 6
 STOP_REL_B, STOP_INITRESID, STOP_RHS = 0, 1, 2
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5
@@ -27,7 +27,7 @@ PROF_SEM, PROF_PCG_APPLY, PROF_PCG_UPDATE, PROF_EXTRAP = 0, 1, 2, 3
 PROF_PROJ_DOTS, PROF_PROJ_LINCOMB, PROF_PROJ_UPDATE = 4, 5, 6
 
 METHOD_NAMES = {"zero": ZERO, "last": LAST, "extrap": EXTRAP, "qr": PROJ_QR,
-                "classic": PROJ_CLASSIC, "spextrap": SPEXTRAP}
+                "classic": PROJ_CLASSIC, "spextrap": SPEXTRAP, "energy": PROJ_ENERGY}
 
 # (name, restype, argtypes) of every exported entry point
 _VP, _I, _D, _I64, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
@@ -245,7 +245,8 @@ class Op:
 
 class Guess:
     """Initial-guess history: ZERO, LAST, EXTRAP(m, s), SPEXTRAP(m, s),
-    QR(s) (Algorithm 2) or CLASSIC(s) (Algorithm 1)."""
+    QR(s) (Algorithm 2), CLASSIC(s) (Algorithm 1) or ENERGY(s) (the QR(s)
+    window in the energy inner product)."""
 
     def __init__(self, n, s, method, m=-1, eps_rel=1e-10, op=None, dtype="f64"):
         torch = _torch()
@@ -295,7 +296,7 @@ class Guess:
         buf = (ctypes.c_double * (self.s * self.s))()
         _check(lib().sg_guess_info(self.h, ctypes.byref(d), buf, _stream()))
         arr = np.array(buf[:])
-        if self.method in (PROJ_QR, PROJ_CLASSIC):
+        if self.method in (PROJ_QR, PROJ_CLASSIC, PROJ_ENERGY):
             return d.value, arr.reshape(self.s, self.s)
         return d.value, arr[:self.s]
 

@@ -137,6 +137,7 @@ struct ProjArgs {
   T* out;            // form: x0
   size_t stride;     // elements between slots
   int n, M, classic;
+  int energy;        // inner products in the A-inner product (A-orthonormal X~)
   double eps_rel;
   ProjState* st;
   double* partials;
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(256) k_proj_dots(const ProjArgs<T> a) {
   double v[NV], tot[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
-#define SG_CALL(D) dots_body<T, D>(a.B, a.stride, a.v, a.n, v)
+  const T* partner = a.energy ? a.X : a.B;   // energy: alpha = X~^T b = (X~, A^{-1} b)_A
+#define SG_CALL(D) dots_body<T, D>(partner, a.stride, a.v, a.n, v)
   SG_COLS_DISPATCH(d, SG_CALL)
 #undef SG_CALL
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
@@ -278,36 +280,40 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
   }
 }
 
-template <typename T, int D>
+template <typename T, int D, bool EN>
 __device__ __forceinline__ void givens_body(const ProjArgs<T>& a, const T* s_sc, const T* s_c, const T* s_s,
                                             const T* s_cin, const T* s_sin, double (&v)[NV]) {
   T acc[SG_NZ(D)];
 #pragma unroll
   for (int j = 0; j < D; ++j) acc[j] = 0;
-  givens_sweep<T, D, true>(a.B, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
-  givens_sweep<T, D, false>(a.X, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
+  // CGS pass-1 dots with the rotated columns: B~ (Euclidean) or X~ (energy)
+  givens_sweep<T, D, !EN>(a.B, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
+  givens_sweep<T, D, EN>(a.X, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
 #pragma unroll
   for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
 }
 
+// u . t (u = t: ||t||^2)
 template <typename T>
-__device__ __forceinline__ T sq_norm(const T* t, int n) {
+__device__ __forceinline__ T vdot(const T* u, const T* t, int n) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   T nn = 0;
   const int nv = n / W, stride_i = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
     const V tv = reinterpret_cast<const V*>(t)[i];
+    const V uv = reinterpret_cast<const V*>(u)[i];
 #pragma unroll
-    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+    for (int w = 0; w < W; ++w) nn += vel(uv, w) * vel(tv, w);
   }
-  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) nn += t[i] * t[i];
+  for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) nn += u[i] * t[i];
   return nn;
 }
 
 // update sweep 1: optional Givens downdate (Algorithm 2, d = M) or classic
-// restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2.
-template <typename T>
+// restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2
+// (energy: c1 = X~^T t = (X~, x_k)_A and ||x_k||_A^2 = x_k . t).
+template <typename T, bool EN>
 __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
@@ -356,15 +362,15 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
   if (rot) {
-#define SG_CALL(D) givens_body<T, D>(a, s_sc, s_c, s_s, s_cin, s_sin, v)
+#define SG_CALL(D) givens_body<T, D, EN>(a, s_sc, s_c, s_s, s_cin, s_sin, v)
     SG_COLS_DISPATCH(d, SG_CALL)
 #undef SG_CALL
   } else {
-#define SG_CALL(D) dots_body<T, D>(a.B, a.stride, a.t, a.n, v)
+#define SG_CALL(D) dots_body<T, D>(EN ? a.X : a.B, a.stride, a.t, a.n, v)
     SG_COLS_DISPATCH(d, SG_CALL)
 #undef SG_CALL
   }
-  v[SG_SMAX] = (double)sq_norm<T>(a.t, a.n);
+  v[SG_SMAX] = (double)vdot<T>(EN ? a.v : a.t, a.t, a.n);
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (tid == 0) {
       ProjState* st = a.st;
@@ -384,8 +390,8 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   }
 }
 
-// t -= sum_j c_j slot_j (D columns), then v[j] = slot_j . t
-template <typename T, int D>
+// t -= sum_j c_j B_j (D columns), then v[j] = B_j . t (energy: X_j . t)
+template <typename T, int D, bool EN>
 __device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[NV]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
@@ -402,26 +408,31 @@ __device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_
     for (int j = 0; j < D; ++j)
 #pragma unroll
       for (int w = 0; w < W; ++w) vel(tv, w) -= c[j] * vel(cols[j], w);
+    if constexpr (EN) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) cols[j] = colv(a.X, a.stride, j)[i];
+    }
 #pragma unroll
     for (int j = 0; j < D; ++j)
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[j] += vel(cols[j], w) * vel(tv, w);
     reinterpret_cast<V*>(a.t)[i] = tv;
   }
+  const T* dotcols = EN ? a.X : a.B;
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     T tt = a.t[i];
 #pragma unroll
     for (int j = 0; j < D; ++j) tt -= c[j] * a.B[(size_t)j * a.stride + i];
 #pragma unroll
-    for (int j = 0; j < D; ++j) acc[j] += a.B[(size_t)j * a.stride + i] * tt;
+    for (int j = 0; j < D; ++j) acc[j] += dotcols[(size_t)j * a.stride + i] * tt;
     a.t[i] = tt;
   }
 #pragma unroll
   for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
 }
 
-// update sweep 2: t -= B~ c1; c2 = B~^T t
-template <typename T>
+// update sweep 2: t -= B~ c1; c2 = B~^T t (energy: X~^T t)
+template <typename T, bool EN>
 __global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   const int d = a.st->d;
@@ -431,7 +442,7 @@ __global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
   double v[NV], tot[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
-#define SG_CALL(D) upd2_body<T, D>(a, c, v)
+#define SG_CALL(D) upd2_body<T, D, EN>(a, c, v)
   SG_COLS_DISPATCH(d, SG_CALL)
 #undef SG_CALL
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
@@ -441,7 +452,8 @@ __global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
 }
 
 // b~ = t - sum c2_j B_j -> Bd; x~ = x - sum cx_j X_j -> Xd; returns ||b~||^2
-template <typename T, int D>
+// (energy: ||x~||_A^2 = x~ . b~)
+template <typename T, int D, bool EN>
 __device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SMAX], const T (&cx)[SG_SMAX],
                                        T* Bd, T* Xd) {
   using V = typename VecT<T>::V;
@@ -462,7 +474,7 @@ __device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SM
       }
     }
 #pragma unroll
-    for (int w = 0; w < W; ++w) nn += vel(tv, w) * vel(tv, w);
+    for (int w = 0; w < W; ++w) nn += vel(EN ? xv : tv, w) * vel(tv, w);
     reinterpret_cast<V*>(Bd)[i] = tv;
     reinterpret_cast<V*>(Xd)[i] = xv;
   }
@@ -473,7 +485,7 @@ __device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SM
       tt -= c2[j] * a.B[(size_t)j * a.stride + i];
       xx -= cx[j] * a.X[(size_t)j * a.stride + i];
     }
-    nn += tt * tt;
+    nn += (EN ? xx : tt) * tt;
     Bd[i] = tt;
     Xd[i] = xx;
   }
@@ -481,8 +493,9 @@ __device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SM
 }
 
 // update sweep 3: b~ = t - B~ c2 -> B~ slot d; x~ = x_k - X~ (c1 + c2) -> X~ slot d;
-// ||b~||^2; acceptance test and R column (Algorithm 2, last block)
-template <typename T>
+// ||b~||^2 (energy: ||x~||_A^2); acceptance test and R column (Algorithm 2,
+// last block)
+template <typename T, bool EN>
 __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   const int d = a.st->d;
@@ -495,7 +508,7 @@ __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   T* Bd = a.B + (size_t)d * a.stride;
   T* Xd = a.X + (size_t)d * a.stride;
   T nn = 0;
-#define SG_CALL(D) nn = upd3_body<T, D>(a, c2, cx, Bd, Xd)
+#define SG_CALL(D) nn = upd3_body<T, D, EN>(a, c2, cx, Bd, Xd)
   SG_COLS_DISPATCH(d, SG_CALL)
 #undef SG_CALL
   double v[NV], tot[NV];
@@ -505,9 +518,11 @@ __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0) {
       ProjState* st = a.st;
-      const double nb = sqrt(tot[SG_SMAX]);
+      // energy: x~ . A x~ can round below zero for a dependent vector
+      const double nb = tot[SG_SMAX] > 0.0 ? sqrt(tot[SG_SMAX]) : 0.0;
       st->nrmsq = tot[SG_SMAX];
-      const bool accept = (d == 0) ? (nb > 0.0) : (nb > a.eps_rel * sqrt(st->nrm0sq));
+      const double nrm0 = st->nrm0sq > 0.0 ? sqrt(st->nrm0sq) : 0.0;
+      const bool accept = (d == 0) ? (nb > 0.0) : (nb > a.eps_rel * nrm0);
       st->accepted = accept ? 1 : 0;
       if (accept && isfinite(nb)) {
         for (int j = 0; j < d; ++j) st->R[j * SG_SMAX + d] = st->c1[j] + st->c2[j];
@@ -533,7 +548,7 @@ __global__ void k_proj_init(ProjState* st) {
 namespace {
 
 bool is_ring(int m) { return m == SG_EXTRAP || m == SG_SPEXTRAP || m == SG_LAST; }
-bool is_proj(int m) { return m == SG_PROJ_QR || m == SG_PROJ_CLASSIC; }
+bool is_proj(int m) { return m == SG_PROJ_QR || m == SG_PROJ_CLASSIC || m == SG_PROJ_ENERGY; }
 
 int reduce_blocks(int64_t n, int W) {
   int64_t b = ((n + W - 1) / W + 255) / 256;
@@ -572,6 +587,7 @@ ProjArgs<T> proj_args(sg_guess_t g) {
   a.n = (int)g->n;
   a.M = g->s;
   a.classic = g->method == SG_PROJ_CLASSIC;
+  a.energy = g->method == SG_PROJ_ENERGY;
   a.eps_rel = g->eps_rel;
   a.st = reinterpret_cast<ProjState*>(g->ws + g->off_state);
   a.partials = reinterpret_cast<double*>(g->ws + g->off_partials);
@@ -638,19 +654,28 @@ int proj_update(sg_guess_t g, const void* x, cudaStream_t s) {
   if (rc) return rc;
   const int nb = reduce_blocks(g->n, VecT<T>::W);
   ProfScope ps(PROF_PROJ_UPDATE, s);
-  k_proj_upd1<T><<<nb, 256, 0, s>>>(a);
-  SG_LAUNCH_CHECK("k_proj_upd1");
-  k_proj_upd2<T><<<nb, 256, 0, s>>>(a);
-  SG_LAUNCH_CHECK("k_proj_upd2");
-  k_proj_upd3<T><<<nb, 256, 0, s>>>(a);
-  SG_LAUNCH_CHECK("k_proj_upd3");
+  if (a.energy) {
+    k_proj_upd1<T, true><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd1");
+    k_proj_upd2<T, true><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd2");
+    k_proj_upd3<T, true><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd3");
+  } else {
+    k_proj_upd1<T, false><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd1");
+    k_proj_upd2<T, false><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd2");
+    k_proj_upd3<T, false><<<nb, 256, 0, s>>>(a);
+    SG_LAUNCH_CHECK("k_proj_upd3");
+  }
   return SG_OK;
 }
 
 }  // namespace
 
 extern "C" size_t sg_guess_workspace_bytes(int64_t n, int s, int method, int dtype) {
-  if (n < 1 || s < 1 || s > SG_SMAX || method < 0 || method > 5 || (dtype != SG_F64 && dtype != SG_F32)) return 0;
+  if (n < 1 || s < 1 || s > SG_SMAX || method < 0 || method > 6 || (dtype != SG_F64 && dtype != SG_F32)) return 0;
   return guess_layout(n, s, method, dtype).total;
 }
 
@@ -660,7 +685,7 @@ extern "C" int sg_guess_create(sg_guess_t* out, int64_t n, int s, int method, in
   *out = nullptr;
   if (n < 1 || n >= (1LL << 31)) return sg_fail(SG_ERR_INVALID, "guess_create: n out of range");
   if (s < 1 || s > SG_SMAX) return sg_fail(SG_ERR_INVALID, "guess_create: s must be in [1, 16]");
-  if (method < 0 || method > 5) return sg_fail(SG_ERR_INVALID, "guess_create: unknown method");
+  if (method < 0 || method > 6) return sg_fail(SG_ERR_INVALID, "guess_create: unknown method");
   if (dtype != SG_F64 && dtype != SG_F32) return sg_fail(SG_ERR_INVALID, "guess_create: bad dtype");
   if (is_proj(method)) {
     if (!op) return sg_fail(SG_ERR_INVALID, "guess_create: projection needs the operator");

@@ -10,7 +10,7 @@ import pytest
 from oracle.sem import SemOperator
 from oracle.pcg import pcg as opcg, REL_B, INITRESID, RHS
 from oracle import extrap as oex
-from oracle.proj import ProjectionQR, ProjectionClassic
+from oracle.proj import ProjectionQR, ProjectionClassic, ProjectionEnergy
 from oracle.sequence import run_sequence
 from synthetic import Modes, random_vectors, CONFIGS
 
@@ -268,7 +268,7 @@ def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dt
         prev.append(x)
         d, R = g.info()
         assert d == o.d, "d at step %d" % k
-        if method == "qr" and dtype == "f64":
+        if method in ("qr", "energy") and dtype == "f64":
             Ro = o.R[:d, :d]
             assert np.allclose(R[:d, :d], Ro, rtol=1e-10, atol=1e-10 * np.abs(Ro).max())
 
@@ -285,6 +285,45 @@ def test_proj_qr_sequence_f32(sg):
 @pytest.mark.parametrize("M", [1, 3, 4])
 def test_proj_classic_sequence(sg, M):
     _proj_sequence(sg, ProjectionClassic, "classic", M)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_proj_energy_sequence(sg, M):
+    """Energy-norm projection (A-orthonormal X~) against the oracle: guesses to
+    1e-12, history size and R through insertions, a rejected dependent vector
+    and Givens downdates."""
+    _proj_sequence(sg, ProjectionEnergy, "energy", M)
+
+
+def test_proj_energy_sequence_f32(sg):
+    _proj_sequence(sg, ProjectionEnergy, "energy", 4, dtype="f32")
+
+
+def test_proj_energy_full_size_galerkin(sg):
+    """16^3 p = 7 FP64 Helmholtz, ENERGY(6) after 8 updates (two downdates): the
+    guess is the A-orthogonal projection of the solution onto the window, so its
+    residual is orthogonal to every window solution (x_j . (b - A x0) = 0), and
+    an in-span right-hand side gives back its solution."""
+    E, p, lam, M = (16, 16, 16), 7, 1e5, 6
+    op = sg.Op(*E, p, lam, "f64")
+    g = sg.Guess(op.n, M, "energy", eps_rel=1e-10, op=op)
+    cx, cy, cz = op.coords_1d()
+    inner = [(c > 0) & (c < 1) for c in (cx, cy, cz)]
+    mask = np.einsum('k,j,i->kji', inner[2], inner[1], inner[0]).reshape(-1).astype(np.float64)
+    rng = np.random.default_rng(31)
+    xs = [dev(rng.standard_normal(op.n) * mask) for _ in range(M + 2)]
+    for x in xs:
+        g.update(x)
+    assert g.info()[0] == M
+    b = op.apply(dev(rng.standard_normal(op.n) * mask))
+    x0 = op.zeros()
+    g.form(b, x0)
+    r = b - op.apply(x0)
+    for xj in xs[2:]:
+        assert abs(float(xj @ r)) <= 1e-10 * float(xj.norm() * b.norm())
+    xin = 0.7 * xs[-1] - 0.4 * xs[-3]
+    g.form(op.apply(xin), x0)
+    assert rel(host(x0), host(xin)) <= 1e-10
 
 
 def test_proj_rejects_dependent_vector(sg):
