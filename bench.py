@@ -596,6 +596,20 @@ def main():
                            "max_relres": max(r["rels"])}
         comp["extrap(2,8)"] = {"ms_per_step": ms_step, "cg_iters_per_step": out["cg_iters_per_step"]}
         out["methods"] = comp
+        # projection kernels of QR(8) with a full history (d = M = 8): kernel-timing
+        # pass as for the headline; algorithmic words per node: guess 2(d+1)
+        # (b and d columns of B~ read; d columns of X~ read, x0 written), update
+        # 7M+2 (upd1 with the Givens downdate 4M-1, upd2 M+1, upd3 2M+2)
+        rq = run_method(sg, torch, wl, "qr", 0, s, args.steps, args.warmup, flush, prof=True)
+        qk = {}
+        for label, kid, words in (("proj_dots", sg.PROF_PROJ_DOTS, s + 1), ("proj_lincomb", sg.PROF_PROJ_LINCOMB, s + 1),
+                                  ("proj_update", sg.PROF_PROJ_UPDATE, 7 * s + 2)):
+            t, c = sg.profile_read(kid)
+            avg = t / max(c, 1)
+            gbs = words * 8 * n / (avg * 1e-3) / 1e9 if c else None
+            qk[label] = {"avg_us": 1e3 * avg, "launch_groups": c, "bytes_per_group": words * 8 * n, "GB_s": gbs,
+                         "frac_of_hbm": gbs / hbm_gbs if gbs else None}
+        out["guess_kernels"]["qr(8)"] = qk
         # the paper's two stopping rules (Eqs. StopCritINITRESID, StopCritRHS) against
         # the workload's ||r|| <= tol ||b||, same EXTRAP(2,8) sequence
         crit = {}

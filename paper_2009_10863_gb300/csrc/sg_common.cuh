@@ -111,68 +111,76 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of NV values per thread (fixed shuffle tree, then a
-// fixed-order combine of warp results).  Result valid in thread 0.
+constexpr int ceil_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+constexpr int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+// Deterministic block sum of NV <= 32 values per thread.  Result valid in
+// thread 0.  Warp stage, for NV >= 2 "transposed": the NV values (padded to
+// NP, a power of two) are halved every exchange -- a lane keeps the upper or
+// the lower half by its lane bit and adds the partner's copy of that half --
+// so after log2(NP) exchanges each lane carries the partial sum of one value
+// and the remaining 5 - log2(NP) exchanges complete it: NP - 1 + 5 - log2(NP)
+// additions per warp instead of 5 NV.  Then warp 0 adds the warp totals in
+// warp order.  A block's last warp, when only partly populated, sums each
+// value with its own shuffle tree instead (its missing lanes hold no results).
+// Summation order is fixed, so results repeat bit for bit.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32*NV */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+  static_assert(NV >= 1 && NV <= 32, "block_sum: 1..32 values");
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int nwarps = (nthreads + 31) >> 5;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int tl = tid & 31, tw = tid >> 5;
-  (void)lane; (void)warp;
+  constexpr int NP = ceil_pow2(NV), L = ilog2(NP), G = 32 >> L;   // lanes per value at the end
+  const bool full = nthreads - tw * 32 >= 32;
+  double t = 0.0;
+  const int j = (tl >> (5 - L)) & (NP - 1);   // value a full warp's lane ends with
+  if (full) {                        // transposed reduction
+    double w[NP];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  __syncthreads();
-  if (tl == 0) {
+    for (int k = 0; k < NP; ++k) w[k] = (k < NV) ? v[k] : 0.0;
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+      const int o = 16 >> r, half = NP >> (r + 1);
+      const bool hi = (tl & o) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const double keep = hi ? w[half + i] : w[i];
+        const double give = hi ? w[i] : w[half + i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+      }
+    }
+    t = w[0];
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  } else {                           // the block's last, partial warp: one tree per value into lane 0
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  }
+  __syncthreads();                   // smem free from any earlier use
+  if (full) {
+    if ((tl & (G - 1)) == 0 && j < NV) smem[j * 32 + tw] = t;
+  } else if (tl == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) smem[k * 32 + tw] = v[k];
   }
   __syncthreads();
   if (tw == 0) {
+    double a = 0.0;
+    if (tl < NV)
+      for (int q = 0; q < nwarps; ++q) a += smem[tl * 32 + q];
+    __syncwarp();
+    if (tl < NV) smem[tl] = a;
+    __syncwarp();
+    if (tl == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double a = (tl < nwarps) ? smem[k * 32 + tl] : 0.0;
-      v[k] = warp_sum(a);
+      for (int k = 0; k < NV; ++k) v[k] = smem[k];
     }
   }
   __syncthreads();
 }
 
-// Deterministic block sum of two values per thread with half the FP64
-// additions of two separate shuffle trees: one exchange at distance 16 leaves
-// partial sums of a in lanes 0-15 and of b in lanes 16-31, and four more rounds
-// reduce one value per lane.  Blocks of at most 512 threads.  Results valid in
-// thread 0 (a and b).
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* smem /* >= 64 */) {
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
-  const int tl = tid & 31, tw = tid >> 5;
-  const bool hi = (tl & 16) != 0;
-  double keep = hi ? b : a;
-  const double give = hi ? a : b;
-  keep += __shfl_xor_sync(0xffffffffu, give, 16);
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
-  __syncthreads();
-  if (tl == 0) smem[tw] = keep;             // warp sum of a
-  if (tl == 16) smem[32 + tw] = keep;       // warp sum of b
-  __syncthreads();
-  if (tw == 0) {
-    const int w = tl & 15;
-    double x = (w < nwarps) ? smem[(hi ? 32 : 0) + w] : 0.0;
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    const double xb = __shfl_sync(0xffffffffu, x, 16);
-    if (tl == 0) { a = x; b = xb; }
-  }
-  __syncthreads();
-}
 
-template <int NV>
-__device__ __forceinline__ void block_sum_any(double (&v)[NV], double* smem) {
-  if constexpr (NV == 2) block_sum2(v[0], v[1], smem);
-  else block_sum<NV>(v, smem);
-}
 
 // Grid-level deterministic reduction: every block writes its NV partial sums
 // to partials[block*NV + k]; the last block to finish sums them in block
@@ -186,7 +194,7 @@ __device__ bool grid_reduce_last(double (&v)[NV], double* partials, unsigned int
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   const int nblocks = gridDim.x * gridDim.y * gridDim.z;
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_sum_any<NV>(v, smem);
+  block_sum<NV>(v, smem);
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
@@ -204,7 +212,7 @@ __device__ bool grid_reduce_last(double (&v)[NV], double* partials, unsigned int
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partials[(size_t)b * NV + k]);
   }
-  block_sum_any<NV>(acc, smem);
+  block_sum<NV>(acc, smem);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = acc[k];
   if (tid == 0) *counter = 0u;

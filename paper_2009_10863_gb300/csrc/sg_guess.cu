@@ -89,6 +89,20 @@ template <typename V> __device__ __forceinline__ V vzero() { V v; for (int w = 0
     case 15: CALL(15); break; case 16: CALL(16); break; default: break;                   \
   }
 
+// The same for the projection kernels, instantiated only up to DMAX columns
+// (DMAX = the history size s rounded up to 4, 8 or 16; d never exceeds s), so a
+// kernel's registers are sized for the largest column count it can meet.
+#define SG_COLS_CASE(DMAX, k, CALL) case k: if constexpr ((k) <= (DMAX)) { CALL(k); } break;
+#define SG_COLS_DISPATCH_UPTO(DMAX, d, CALL)                                              \
+  switch (d) {                                                                            \
+    SG_COLS_CASE(DMAX, 0, CALL) SG_COLS_CASE(DMAX, 1, CALL) SG_COLS_CASE(DMAX, 2, CALL)    \
+    SG_COLS_CASE(DMAX, 3, CALL) SG_COLS_CASE(DMAX, 4, CALL) SG_COLS_CASE(DMAX, 5, CALL)    \
+    SG_COLS_CASE(DMAX, 6, CALL) SG_COLS_CASE(DMAX, 7, CALL) SG_COLS_CASE(DMAX, 8, CALL)    \
+    SG_COLS_CASE(DMAX, 9, CALL) SG_COLS_CASE(DMAX, 10, CALL) SG_COLS_CASE(DMAX, 11, CALL)  \
+    SG_COLS_CASE(DMAX, 12, CALL) SG_COLS_CASE(DMAX, 13, CALL) SG_COLS_CASE(DMAX, 14, CALL) \
+    SG_COLS_CASE(DMAX, 15, CALL) SG_COLS_CASE(DMAX, 16, CALL) default: break;              \
+  }
+
 // ---------------------------------------------------------------- extrapolation
 template <typename T>
 struct ExtrapArgs {
@@ -151,8 +165,8 @@ __device__ __forceinline__ const typename VecT<T>::V* colv(const T* base, size_t
 #define SG_NZ(D) ((D) > 0 ? (D) : 1)
 
 // v[j] += slot_j . y for j < D (plain dots; the caller applies column scales)
-template <typename T, int D>
-__device__ __forceinline__ void dots_body(const T* base, size_t stride, const T* y, int n, double (&v)[NV]) {
+template <typename T, int D, int N>
+__device__ __forceinline__ void dots_body(const T* base, size_t stride, const T* y, int n, double (&v)[N]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   T acc[SG_NZ(D)];
@@ -177,18 +191,18 @@ __device__ __forceinline__ void dots_body(const T* base, size_t stride, const T*
 }
 
 // form, pass 1: alpha_j = scale_j * (slot_j . b), j < d
-template <typename T>
+template <typename T, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_dots(const ProjArgs<T> a) {
-  __shared__ double sred[32 * NV];
+  __shared__ double sred[32 * SG_SMAX];
   const int d = a.st->d;
-  double v[NV], tot[NV];
+  double v[SG_SMAX], tot[SG_SMAX];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
   const T* partner = a.energy ? a.X : a.B;   // energy: alpha = X~^T b = (X~, A^{-1} b)_A
 #define SG_CALL(D) dots_body<T, D>(partner, a.stride, a.v, a.n, v)
-  SG_COLS_DISPATCH(d, SG_CALL)
+  SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
-  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  if (grid_reduce_last<SG_SMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->alpha[j] = a.st->scale[j] * tot[j];
   }
@@ -220,7 +234,7 @@ __device__ __forceinline__ void lincomb_body(const T* base, size_t stride, const
 }
 
 // form, pass 2: x0 = sum_j alpha_j scale_j slot_j of X~ (x0 untouched if d = 0)
-template <typename T>
+template <typename T, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_lincomb(const ProjArgs<T> a) {
   const int d = a.st->d;
   if (d == 0) return;
@@ -228,7 +242,7 @@ __global__ void __launch_bounds__(256) k_proj_lincomb(const ProjArgs<T> a) {
 #pragma unroll
   for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->alpha[j] * a.st->scale[j]) : (T)0;
 #define SG_CALL(D) lincomb_body<T, D>(a.X, a.stride, c, a.out, a.n)
-  SG_COLS_DISPATCH(d, SG_CALL)
+  SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
 }
 
@@ -313,7 +327,7 @@ __device__ __forceinline__ T vdot(const T* u, const T* t, int n) {
 // update sweep 1: optional Givens downdate (Algorithm 2, d = M) or classic
 // restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2
 // (energy: c1 = X~^T t = (X~, x_k)_A and ||x_k||_A^2 = x_k . t).
-template <typename T, bool EN>
+template <typename T, bool EN, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
@@ -363,11 +377,11 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
   if (rot) {
 #define SG_CALL(D) givens_body<T, D, EN>(a, s_sc, s_c, s_s, s_cin, s_sin, v)
-    SG_COLS_DISPATCH(d, SG_CALL)
+    SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
   } else {
 #define SG_CALL(D) dots_body<T, D>(EN ? a.X : a.B, a.stride, a.t, a.n, v)
-    SG_COLS_DISPATCH(d, SG_CALL)
+    SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
   }
   v[SG_SMAX] = (double)vdot<T>(EN ? a.v : a.t, a.t, a.n);
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
 
 // t -= sum_j c_j B_j (D columns), then v[j] = B_j . t (energy: X_j . t)
 template <typename T, int D, bool EN>
-__device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[NV]) {
+__device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[SG_SMAX]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   T acc[SG_NZ(D)];
@@ -432,20 +446,20 @@ __device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_
 }
 
 // update sweep 2: t -= B~ c1; c2 = B~^T t (energy: X~^T t)
-template <typename T, bool EN>
+template <typename T, bool EN, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
-  __shared__ double sred[32 * NV];
+  __shared__ double sred[32 * SG_SMAX];
   const int d = a.st->d;
   T c[SG_SMAX];
 #pragma unroll
   for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->c1[j] * a.st->scale[j]) : (T)0;
-  double v[NV], tot[NV];
+  double v[SG_SMAX], tot[SG_SMAX];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
 #define SG_CALL(D) upd2_body<T, D, EN>(a, c, v)
-  SG_COLS_DISPATCH(d, SG_CALL)
+  SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
-  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  if (grid_reduce_last<SG_SMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->c2[j] = a.st->scale[j] * tot[j];
   }
@@ -495,7 +509,7 @@ __device__ __forceinline__ T upd3_body(const ProjArgs<T>& a, const T (&c2)[SG_SM
 // update sweep 3: b~ = t - B~ c2 -> B~ slot d; x~ = x_k - X~ (c1 + c2) -> X~ slot d;
 // ||b~||^2 (energy: ||x~||_A^2); acceptance test and R column (Algorithm 2,
 // last block)
-template <typename T, bool EN>
+template <typename T, bool EN, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   const int d = a.st->d;
@@ -509,18 +523,15 @@ __global__ void __launch_bounds__(256) k_proj_upd3(const ProjArgs<T> a) {
   T* Xd = a.X + (size_t)d * a.stride;
   T nn = 0;
 #define SG_CALL(D) nn = upd3_body<T, D, EN>(a, c2, cx, Bd, Xd)
-  SG_COLS_DISPATCH(d, SG_CALL)
+  SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
-  double v[NV], tot[NV];
-#pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
-  v[SG_SMAX] = (double)nn;
-  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  double v[1] = {(double)nn}, tot[1];
+  if (grid_reduce_last<1>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0) {
       ProjState* st = a.st;
       // energy: x~ . A x~ can round below zero for a dependent vector
-      const double nb = tot[SG_SMAX] > 0.0 ? sqrt(tot[SG_SMAX]) : 0.0;
-      st->nrmsq = tot[SG_SMAX];
+      const double nb = tot[0] > 0.0 ? sqrt(tot[0]) : 0.0;
+      st->nrmsq = tot[0];
       const double nrm0 = st->nrm0sq > 0.0 ? sqrt(st->nrm0sq) : 0.0;
       const bool accept = (d == 0) ? (nb > 0.0) : (nb > a.eps_rel * nrm0);
       st->accepted = accept ? 1 : 0;
@@ -635,14 +646,29 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
   const int nb = reduce_blocks(g->n, VecT<T>::W);
   {
     ProfScope ps(PROF_PROJ_DOTS, s);
-    k_proj_dots<T><<<nb, 256, 0, s>>>(a);
+    if (g->s <= 4) k_proj_dots<T, 4><<<nb, 256, 0, s>>>(a);
+    else if (g->s <= 8) k_proj_dots<T, 8><<<nb, 256, 0, s>>>(a);
+    else k_proj_dots<T, 16><<<nb, 256, 0, s>>>(a);
     SG_LAUNCH_CHECK("k_proj_dots");
   }
   {
     ProfScope ps(PROF_PROJ_LINCOMB, s);
-    k_proj_lincomb<T><<<nb * 2, 256, 0, s>>>(a);
+    if (g->s <= 4) k_proj_lincomb<T, 4><<<nb * 2, 256, 0, s>>>(a);
+    else if (g->s <= 8) k_proj_lincomb<T, 8><<<nb * 2, 256, 0, s>>>(a);
+    else k_proj_lincomb<T, 16><<<nb * 2, 256, 0, s>>>(a);
     SG_LAUNCH_CHECK("k_proj_lincomb");
   }
+  return SG_OK;
+}
+
+template <typename T, bool EN, int DMAX>
+int proj_update_sweeps(const ProjArgs<T>& a, int nb, cudaStream_t s) {
+  k_proj_upd1<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd1");
+  k_proj_upd2<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd2");
+  k_proj_upd3<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  SG_LAUNCH_CHECK("k_proj_upd3");
   return SG_OK;
 }
 
@@ -655,21 +681,13 @@ int proj_update(sg_guess_t g, const void* x, cudaStream_t s) {
   const int nb = reduce_blocks(g->n, VecT<T>::W);
   ProfScope ps(PROF_PROJ_UPDATE, s);
   if (a.energy) {
-    k_proj_upd1<T, true><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd1");
-    k_proj_upd2<T, true><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd2");
-    k_proj_upd3<T, true><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd3");
-  } else {
-    k_proj_upd1<T, false><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd1");
-    k_proj_upd2<T, false><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd2");
-    k_proj_upd3<T, false><<<nb, 256, 0, s>>>(a);
-    SG_LAUNCH_CHECK("k_proj_upd3");
+    if (g->s <= 4) return proj_update_sweeps<T, true, 4>(a, nb, s);
+    if (g->s <= 8) return proj_update_sweeps<T, true, 8>(a, nb, s);
+    return proj_update_sweeps<T, true, 16>(a, nb, s);
   }
-  return SG_OK;
+  if (g->s <= 4) return proj_update_sweeps<T, false, 4>(a, nb, s);
+  if (g->s <= 8) return proj_update_sweeps<T, false, 8>(a, nb, s);
+  return proj_update_sweeps<T, false, 16>(a, nb, s);
 }
 
 }  // namespace
