@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic import BATCHED, BATCHED_COMMON, CONFIGS, Modes, noise  # noqa: E402
+from synthetic import forcing_basis_indices, adjoint_parameters, BATCHED, BATCHED_COMMON, CONFIGS, Modes, noise  # noqa: E402
 
 METRIC = "ms per time-step solve at 1e-10 rel. residual + CG iters; guess-kernel HBM GB/s"
 CFG = CONFIGS["c2"]
@@ -224,6 +224,71 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
     return {"ms": sum(ms_steps) / len(ms_steps), "iters": sum(its) / len(its), "max_relres": max(rels),
             "outer": (sum(outs) / len(outs)) if outs else None,
             "extrap_avg_ms": ex_ms / max(ex_cnt, 1), "kernels": kern}
+
+
+def run_adjoint(sg, torch, device, steps):
+    """One loss + gradient evaluation of the time-stepped Helmholtz sequence
+    (16^3 p = 7, lambda = 1e5, 64 forcing modes, EXTRAP(2,6) guesses in both
+    directions, checkpoints every 10 steps) through ``SequenceLoss``: forward
+    solves, then backward (segment recomputation + reverse-time adjoint solves).
+    Targets come from a forward run with theta*; the gradient is taken at
+    theta = theta*/2.  Timed with CUDA events after one untimed evaluation."""
+    from paper_2009_10863_gb300.adjoint import HeatSequence, SequenceLoss
+    c = CONFIGS["c5"]
+    E, p, lam, dt, nparam = c["E"], c["p"], c["lam"], c["dt"], c["modes"]
+    seq = HeatSequence(*E, p, tol=c["tol"], s=c["s"], m=2, checkpoint=10)
+    op = seq.op(lam)
+    cx, cy, cz = op.coords_1d()
+    inner = [(v > 0) & (v < 1) for v in (cx, cy, cz)]
+    idx = forcing_basis_indices(nparam)
+    phi = torch.empty((nparam, op.n), dtype=torch.float64, device=device)
+    for j, (a, b_, cc) in enumerate(idx):
+        f = np.einsum('k,y,x->kyx', np.sin(np.pi * cc * cz) * inner[2], np.sin(np.pi * b_ * cy) * inner[1],
+                      np.sin(np.pi * a * cx) * inner[0]).reshape(-1)
+        phi[j].copy_(torch.from_numpy(f))
+    theta_star, w = adjoint_parameters(5, nparam)
+    C = torch.from_numpy(np.cos(np.outer(dt * np.arange(1, steps + 1), w))).to(device)
+    Fstar = (C * torch.from_numpy(theta_star).to(device)) @ phi
+    # targets: the forward solutions for theta*
+    xs, x_prev = [], None
+    g = sg.Guess(op.n, c["s"], "extrap", m=2)
+    rhs = op.empty()
+    for k in range(steps):
+        sg.lib().sg_mass_rhs(op.h, float(lam), sg._ptr(x_prev) if x_prev is not None else None,
+                             sg._ptr(Fstar[k]), sg._ptr(rhs), sg._stream())
+        x = g.next_slot()
+        g.form(rhs, x)
+        op.pcg(rhs, x, c["tol"], true_residual=False)
+        g.update(x)
+        xs.append(x.clone())
+        x_prev = xs[-1]
+    Xs = torch.stack(xs)
+    del xs, Fstar
+    lam_t = torch.tensor(lam, dtype=torch.float64, device=device, requires_grad=True)
+    res = {}
+    for rep in range(2):
+        theta = torch.from_numpy(0.5 * theta_star).to(device).requires_grad_(True)
+        lam_t.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        L = SequenceLoss.apply((C * theta) @ phi, lam_t, Xs, seq)
+        e1.record()
+        L.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        if rep == 1:
+            it = seq.last_iters
+            res = {"steps": steps, "params": nparam + 1, "checkpoint_every": 10,
+                   "forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2),
+                   "total_ms": e0.elapsed_time(e2),
+                   "ms_per_solve": e0.elapsed_time(e2) / (3 * steps),
+                   "cg_iters_per_solve": {"forward": sum(it["forward"]) / len(it["forward"]),
+                                          "recompute": sum(it["recompute"]) / len(it["recompute"]),
+                                          "adjoint": sum(it["adjoint"]) / len(it["adjoint"])},
+                   "loss": float(L.detach()), "grad_norm_theta": float(theta.grad.norm()),
+                   "dL_dlambda": float(lam_t.grad)}
+    return res
 
 
 def run_batched(sg, torch, device, steps, warmup, flush, mode, tune=True):
@@ -468,6 +533,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sequences comparison")
     ap.add_argument("--batched-steps", type=int, default=8)
     ap.add_argument("--batched-warmup", type=int, default=8)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (loss + gradient) timing")
+    ap.add_argument("--adjoint-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
@@ -659,6 +726,12 @@ def main():
             "steps": args.batched_steps, "warmup": args.batched_warmup,
             "batched_persistent": rb, "sequential_solves": rs,
             "speedup_batched_vs_sequential": rs["ms_per_step"] / rb["ms_per_step"]}
+
+    if not args.no_adjoint:
+        torch.cuda.empty_cache()
+        out["adjoint"] = dict(workload="time-stepped Helmholtz 16^3 p=7, lambda=1e5, 64 forcing modes, "
+                                       "EXTRAP(2,6), 1e-10; loss + gradient in theta (64) and lambda",
+                              **run_adjoint(sg, torch, device, args.adjoint_steps))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, its, _, ns = oracle_sample(out["cg_iters_per_step"], samples=3)
