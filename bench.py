@@ -75,28 +75,30 @@ def sem_flops_per_node(p):
 
 # ------------------------------------------------------------------ clocks
 class Clocks:
+    """nvidia-smi clock and throttle-reason samples every 50 ms (kept in memory)."""
+
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
-        """Start sampling every 50 ms; returns once the first sample is written."""
+        """Start sampling; returns once the first sample has arrived."""
+        self.window = None
+        self.lines = []
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
                                           "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
-            t0 = time.time()
-            while time.time() - t0 < 10 and os.path.getsize(self.path) == 0:
-                time.sleep(0.02)
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            first = self.proc.stdout.readline()      # blocks until nvidia-smi has sampled once
+            if first:
+                self.lines.append(first)
+            else:
+                self.proc = None
         except Exception:
             self.proc = None
-        self.window = None
 
     def mark(self, t0, t1):
         """Host wall-clock interval of the timed region."""
@@ -107,13 +109,14 @@ class Clocks:
             return None
         self.proc.terminate()
         try:
-            self.proc.wait(timeout=5)
+            out, _ = self.proc.communicate(timeout=5)
         except Exception:
             self.proc.kill()
-        self.f.close()
+            out, _ = self.proc.communicate()
+        self.lines.extend((out or "").splitlines())
         rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

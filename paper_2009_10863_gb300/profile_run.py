@@ -6,11 +6,11 @@ mesh of the bench's shapes, for profiling (ncu) and quick timing.
 
 The first form applies the operator `--reps` times (timed with CUDA events),
 runs a few PCG iterations (host-launched, as with kernel timing on), forms an
-EXTRAP(2,8) guess and performs QR(8) history updates.  The second runs time steps of the bench's headline sequence
-(FP64 16^3 p = 7 Helmholtz, EXTRAP(2,8), 1e-10) with every library launch timed
-by CUDA events, so that the PCG iterations are host launches that a
-profiler lists one by one (the bench's timed steps run them inside CUDA-graph
-WHILE loops) -- the workload of the committed launch list.
+EXTRAP(2,8) guess and performs QR(8) history updates.  The second runs time
+steps of bench.py's main sequence (FP64 16^3 p = 7 Helmholtz, EXTRAP(2,8),
+1e-10) with every library launch timed by CUDA events, so that the PCG
+iterations are host launches that a profiler lists one by one (bench.py's
+timed steps run them inside CUDA-graph WHILE loops).
 """
 import argparse
 
@@ -34,7 +34,7 @@ def main():
     from paper_2009_10863_gb300 import build
     build.build()
     if args.steps > 0:
-        return headline_steps(args.steps)
+        return sequence_steps(args.steps)
     E = args.elements
     op = sg.Op(E, E, E, args.p, args.lam, args.dtype)
     gen = torch.Generator(device="cuda").manual_seed(0)
@@ -67,7 +67,7 @@ def main():
           (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, q.info()[0]))
 
 
-def headline_steps(steps):
+def sequence_steps(steps):
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
