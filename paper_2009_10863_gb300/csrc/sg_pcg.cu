@@ -881,7 +881,7 @@ extern "C" int sg_ir_solve_ru(sg_op_t op64, sg_op_t op32, const void* b, void* x
                                                             reinterpret_cast<double*>(ws32 + I.L32.partials));
       SG_LAUNCH_CHECK("k_ru_restart");
     }
-    if (!exec) exec = iteration_graph<float>(op32, ws32, I.L32);
+    if (!exec && !sg_profiling_on()) exec = iteration_graph<float>(op32, ws32, I.L32);
     if (exec) {
       SG_CUDA_TRY(cudaGraphLaunch(exec, s));
     } else {
