@@ -80,3 +80,24 @@ def test_workspace_queries(sg):
     assert L.sg_guess_workspace_bytes(n, 17, sg.EXTRAP, sg.F64) == 0
     assert L.sg_guess_workspace_bytes(n, 8, 9, sg.F64) == 0
     assert L.sg_guess_workspace_bytes(0, 8, sg.EXTRAP, sg.F64) == 0
+
+
+def test_argument_errors_without_a_device(sg):
+    """Entry points reject bad arguments before any device work (so this runs
+    on a host without a GPU) and say why."""
+    L = sg.lib()
+    VP = ctypes.c_void_p
+    assert L.sg_pcg_solve_async(None, VP(16), VP(32), 1e-10, 10, 0, VP(256), None) == sg.ERR_INVALID
+    assert b"NULL" in L.sg_last_error()
+    assert L.sg_pcg_result(None, VP(256), None, None) == sg.ERR_INVALID
+    assert L.sg_ir_solve_ru(None, None, VP(16), VP(32), 1e-10, 0.1, 5, 100, VP(256), None, None, None,
+                            None) == sg.ERR_INVALID
+    h = ctypes.c_void_p()
+    assert L.sg_guess_create(ctypes.byref(h), 1000, 8, sg.PROJ_ENERGY, -1, 1e-10, None, VP(256),
+                             sg.F64) == sg.ERR_INVALID
+    assert b"operator" in L.sg_last_error()
+    assert L.sg_guess_create(ctypes.byref(h), 1000, 8, 7, -1, 1e-10, None, VP(256), sg.F64) == sg.ERR_INVALID
+    n = 4321
+    assert L.sg_guess_workspace_bytes(n, 8, sg.PROJ_ENERGY, sg.F64) == L.sg_guess_workspace_bytes(n, 8, sg.PROJ_QR,
+                                                                                                   sg.F64)
+    assert L.sg_guess_workspace_bytes(n, 8, 7, sg.F64) == 0
