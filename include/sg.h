@@ -17,7 +17,12 @@
  *  - Workspaces are DEVICE buffers owned by the caller, sized by the matching
  *    *_workspace_bytes() query, 256-byte aligned, and must outlive the handle
  *    (guess) or the call (PCG).  The library allocates only the small
- *    per-operator coefficient tables (sg_op_create, < 4 KB).
+ *    per-operator coefficient tables (sg_op_create, < 4 KB), the instantiated
+ *    PCG iteration graphs it caches on an operator (at most 8 per operator,
+ *    released by sg_op_destroy) and one pinned host word per host thread for
+ *    convergence polls.
+ *  - A handle is used by one host thread at a time; different handles may be
+ *    used concurrently.
  *  - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Every call is stream-ordered and asynchronous unless stated.
  *  - Return value: SG_OK (0) on success, SG_NOT_CONVERGED (1) as a warning,
