@@ -155,6 +155,39 @@ __host__ __device__ inline void build_eotab(const SemGeom& g, int d, double mul,
   for (int l = 0; l <= P; ++l) t.crow[l] = (T)(mul * Cm[P][l]);
 }
 
+// The tables of all three directions (build_eotab with mul = 1, the mass term
+// c_m added to z), each entry computed by its own thread: a CTA's set-up costs
+// a few FP64 operations per thread instead of the whole table on one thread.
+template <typename T, int P>
+__device__ __forceinline__ void build_eotabs_par(const SemGeom& g, EOTab<T, P>* tabs, int tid, int nthreads) {
+  using TL = SemTile<P>;
+  constexpr int H = TL::H, HE = TL::HE;
+  constexpr int NCE = HE * H, NCO = H * H, NCM = HE, NCR = P + 1;
+  constexpr int PER = NCE + NCO + NCM + NCR;
+  for (int q = tid; q < 3 * PER; q += nthreads) {
+    const int d = q / PER;
+    int r = q - d * PER;
+    const double dadd = (d == 2) ? g.cm : 0.0;
+    auto Cm = [&](int a, int l) {
+      return g.C[d][a][l] + ((a == l) ? ((a == 0 || a == P) ? 0.5 * dadd : dadd) : 0.0);
+    };
+    EOTab<T, P>& t = tabs[d];
+    if (r < NCE) {
+      const int a = r / H, l = r - (r / H) * H, aa = (a < H) ? a : P / 2;
+      t.ce[a][l] = (T)(0.5 * (Cm(aa, l) + Cm(aa, P - l)));
+    } else if ((r -= NCE) < NCO) {
+      const int a = r / H, l = r - (r / H) * H;
+      t.co[a][l] = (T)(0.5 * (Cm(a, l) - Cm(a, P - l)));
+    } else if ((r -= NCO) < NCM) {
+      const int aa = (r < H) ? r : P / 2;
+      t.cm[r] = TL::MID ? (T)Cm(aa, P / 2) : (T)0;
+    } else {
+      r -= NCM;
+      t.crow[r] = (T)Cm(P, r);
+    }
+  }
+}
+
 // One direction's line product: FP64 reads the scaled table of the direction
 // from shared memory; FP32 uses the unscaled register table times a_d.
 template <typename T, int P, bool CREG>
@@ -213,7 +246,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
   __syncthreads();                               // shared memory of a previous item is free
-  if (tid < 3) build_eotab<T, P>(g, tid, 1.0, sTab[tid], tid == 2 ? g.cm : 0.0);   // mass term in z
+  build_eotabs_par<T, P>(g, sTab, tid, NT);     // x, y, z tables (mass term in z), one entry per thread
   if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
   if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
