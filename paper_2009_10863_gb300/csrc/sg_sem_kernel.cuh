@@ -227,8 +227,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Used by k_sem (one item per CTA) and by the persistent batched kernel.
 template <typename T, int P, int MODE>
 __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, int bxi, int byi, int e0, int e1,
-                                         const T* beta_s, const int* first_s, T (&red)[3]) {
-  // beta_s, first_s: shared-memory scalars of the PCG step (MODE 1), read at use
+                                         const T* beta_s, const int* first_s, T (&red)[3],
+                                         const int* skip_s = nullptr, bool lead_sync = true) {
+  // beta_s, first_s: shared-memory scalars of the PCG step (MODE 1), read at use.
+  // skip_s: shared flag written before the call (the set-up barrier publishes
+  // it); the item returns at once when it is set.  lead_sync = false: no earlier
+  // item used this CTA's shared memory (k_sem), so the leading barrier is omitted.
   using TL = SemTile<P>;
   constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL;
   constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
@@ -245,11 +249,12 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  __syncthreads();                               // shared memory of a previous item is free
+  if (lead_sync) __syncthreads();                // shared memory of a previous item is free
   build_eotabs_par<T, P>(g, sTab, tid, NT);     // x, y, z tables (mass term in z), one entry per thread
   if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
   if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
+  if (skip_s && *skip_s) return;
 
   const int x0 = bxi * TX, y0 = byi * TY;
   const size_t nxy = (size_t)g.nx * g.ny;
@@ -461,17 +466,16 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   __shared__ T s_beta;
   __shared__ int s_first;
   const int tid = threadIdx.x + SemTile<P>::TX * threadIdx.y;
-  if (tid == 0) {
+  if (tid == 0) {             // published by the table set-up barrier inside sem_item
     s_skip = (MODE == 1) ? a.st->done : 0;
     s_beta = (MODE == 1) ? (T)a.st->beta : (T)0;
     s_first = (MODE == 1) ? a.st->first : 1;
   }
-  __syncthreads();
-  if (MODE == 1 && s_skip) return;
   T red[3] = {(T)0, (T)0, (T)0};
   const int e0 = blockIdx.z * a.zl;
   const int e1 = min(g.ez, e0 + a.zl);
-  sem_item<T, P, MODE>(g, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red);
+  sem_item<T, P, MODE>(g, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red, &s_skip, false);
+  if (MODE == 1 && s_skip) return;
 
   if (MODE == 1) {
     double v[1] = {(double)red[0]}, tot[1];
