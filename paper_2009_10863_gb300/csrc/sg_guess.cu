@@ -249,45 +249,86 @@ __global__ void __launch_bounds__(256) k_proj_lincomb(const ProjArgs<T> a) {
 // One Givens sweep over a column set (App. A: the column shared by successive
 // rotations stays in registers): D rotations, new columns 0..D-1 written back,
 // dots of the new B~ columns with t accumulated when DOTS.
-template <typename T, int D, bool DOTS>
-__device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t, int n, T sc0, const T* gc,
-                                             const T* gs, const T* gcin, const T* gsin, T (&acc)[SG_NZ(D)]) {
+//
+// The rotations are normally applied in factored ("fast Givens", Gentleman
+// 1973) form on unscaled columns: a rotation of the pair (C, N) with column
+// scales (sc, sn) -- true columns sc C, sn N -- writes new = X + k1 Y and
+// carries X' = Y + k2 X (one multiply-add each, X/Y = C/N or N/C as gr.swap
+// says), the factor taken out going into the column scales; thread 0 of the
+// block computes k1, k2, swap and the scales from c and s (k_proj_upd1).  That
+// is half the FP64 operations of applying c and s directly.  The scales drift
+// by the factors taken out, so once one leaves a safe range the sweep runs in
+// the plain form instead, new = q0 C + q1 N, carry = q2 C + q3 N on a carry
+// that starts as sc0 C, which leaves every new column with scale 1.
+template <typename T>
+struct GivensCoef {
+  T k1[SG_SMAX], k2[SG_SMAX];   // factored form
+  int swap[SG_SMAX];
+  T q[4][SG_SMAX];              // plain form
+  T sc0;
+};
+
+template <typename T, int D, bool DOTS, bool FAST>
+__device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t, int n, const GivensCoef<T>& gr,
+                                             T (&acc)[SG_NZ(D)]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   const int nv = n / W, stride_i = gridDim.x * blockDim.x;
-  // rotation coefficients stay in shared memory (block-uniform broadcast reads)
-  const T* cc = gc;
-  const T* ss = gs;
-  const T* ci = gcin;
-  const T* si = gsin;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
     V tv;
     if (DOTS) tv = reinterpret_cast<const V*>(t)[i];
     V carry = reinterpret_cast<const V*>(base)[i];
+    if (!FAST) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) vel(carry, w) *= sc0;
+      for (int w = 0; w < W; ++w) vel(carry, w) *= gr.sc0;
+    }
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const V nx = colv(base, stride, j + 1)[i];
       V o;
+      if (FAST) {
+        const bool sw = gr.swap[j] != 0;
+        const T k1 = gr.k1[j], k2 = gr.k2[j];
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const T cw = vel(carry, w), nw = vel(nx, w);
-        vel(o, w) = cc[j] * cw + si[j] * nw;
-        vel(carry, w) = -ss[j] * cw + ci[j] * nw;
-        if (DOTS) acc[j] += vel(o, w) * vel(tv, w);
+        for (int w = 0; w < W; ++w) {
+          const T x = sw ? vel(nx, w) : vel(carry, w);
+          const T y = sw ? vel(carry, w) : vel(nx, w);
+          vel(o, w) = fma(k1, y, x);
+          vel(carry, w) = fma(k2, x, y);
+        }
+      } else {
+        const T q0 = gr.q[0][j], q1 = gr.q[1][j], q2 = gr.q[2][j], q3 = gr.q[3][j];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const T cv = vel(carry, w), nv_ = vel(nx, w);
+          vel(o, w) = q0 * cv + q1 * nv_;
+          vel(carry, w) = q2 * cv + q3 * nv_;
+        }
+      }
+      if (DOTS) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j] += vel(o, w) * vel(tv, w);
       }
       reinterpret_cast<V*>(base + (size_t)j * stride)[i] = o;
     }
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
     const T tt = DOTS ? t[i] : (T)0;
-    T carry = sc0 * base[i];
+    T carry = base[i];
+    if (!FAST) carry *= gr.sc0;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const T nx = base[(size_t)(j + 1) * stride + i];
-      const T o = cc[j] * carry + si[j] * nx;
-      carry = -ss[j] * carry + ci[j] * nx;
+      T o;
+      if (FAST) {
+        const bool sw = gr.swap[j] != 0;
+        const T x = sw ? nx : carry, y = sw ? carry : nx;
+        o = fma(gr.k1[j], y, x);
+        carry = fma(gr.k2[j], x, y);
+      } else {
+        o = gr.q[0][j] * carry + gr.q[1][j] * nx;
+        carry = gr.q[2][j] * carry + gr.q[3][j] * nx;
+      }
       if (DOTS) acc[j] += o * tt;
       base[(size_t)j * stride + i] = o;
     }
@@ -295,14 +336,19 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
 }
 
 template <typename T, int D, bool EN>
-__device__ __forceinline__ void givens_body(const ProjArgs<T>& a, const T* s_sc, const T* s_c, const T* s_s,
-                                            const T* s_cin, const T* s_sin, double (&v)[NV]) {
+__device__ __forceinline__ void givens_body(const ProjArgs<T>& a, const GivensCoef<T>& gr, bool fast,
+                                            double (&v)[NV]) {
   T acc[SG_NZ(D)];
 #pragma unroll
   for (int j = 0; j < D; ++j) acc[j] = 0;
   // CGS pass-1 dots with the rotated columns: B~ (Euclidean) or X~ (energy)
-  givens_sweep<T, D, !EN>(a.B, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
-  givens_sweep<T, D, EN>(a.X, a.stride, a.t, a.n, s_sc[0], s_c, s_s, s_cin, s_sin, acc);
+  if (fast) {
+    givens_sweep<T, D, !EN, true>(a.B, a.stride, a.t, a.n, gr, acc);
+    givens_sweep<T, D, EN, true>(a.X, a.stride, a.t, a.n, gr, acc);
+  } else {
+    givens_sweep<T, D, !EN, false>(a.B, a.stride, a.t, a.n, gr, acc);
+    givens_sweep<T, D, EN, false>(a.X, a.stride, a.t, a.n, gr, acc);
+  }
 #pragma unroll
   for (int j = 0; j < D; ++j) v[j] = (double)acc[j];
 }
@@ -331,8 +377,9 @@ template <typename T, bool EN, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
-  __shared__ T s_cin[SG_SMAX], s_sin[SG_SMAX], s_c[SG_SMAX], s_s[SG_SMAX], s_sc[SG_SMAX];
-  __shared__ int s_d, s_rot;
+  __shared__ GivensCoef<T> gr;
+  __shared__ double s_scale[SG_SMAX];   // column scales after the downdate
+  __shared__ int s_d, s_rot, s_fast;
   const int tid = threadIdx.x;
   if (tid == 0) {
     const ProjState* st = a.st;
@@ -345,6 +392,17 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
       // R <- R(:, 2:d): a d x (d-1) upper Hessenberg matrix
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d - 1; ++j) sR[i * SG_SMAX + j] = st->R[i * SG_SMAX + j + 1];
+      // factored form while every scale stays within 2^-e..2^e (stored
+      // values then stay far from overflow and underflow in T)
+      const double lim = sizeof(T) == 8 ? 0x1p300 : 0x1p40;
+      int fast = 1;
+      for (int j = 0; j < d; ++j) {
+        const double m = fabs(st->scale[j]);
+        if (!(m < lim && m > 1.0 / lim)) fast = 0;
+      }
+      s_fast = fast;
+      gr.sc0 = (T)st->scale[0];
+      double sc = st->scale[0];   // scale of the stored carry column
       for (int i = 0; i < d - 1; ++i) {
         double av = sR[i * SG_SMAX + i], bv = sR[(i + 1) * SG_SMAX + i];
         double r = hypot(av, bv);
@@ -355,14 +413,33 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
           sR[i * SG_SMAX + j] = c * u + s * w;
           sR[(i + 1) * SG_SMAX + j] = -s * u + c * w;
         }
-        // new_i = c L_i + s L_{i+1}, carry = -s L_i + c L_{i+1}; the incoming
-        // physical slot i+1 carries its column scale
-        s_c[i] = (T)c;
-        s_s[i] = (T)s;
-        s_cin[i] = (T)(c * st->scale[i + 1]);
-        s_sin[i] = (T)(s * st->scale[i + 1]);
+        // new_i = c L_i + s L_{i+1}, carry = -s L_i + c L_{i+1} on the true
+        // columns L = scale * stored.  Plain form: the carry holds true
+        // values, the incoming stored column N has scale sn.
+        const double sn = st->scale[i + 1];
+        gr.q[0][i] = (T)c;
+        gr.q[1][i] = (T)(s * sn);
+        gr.q[2][i] = (T)(-s);
+        gr.q[3][i] = (T)(c * sn);
+        // Factored form: stored carry C has scale sc.  Taking out the larger
+        // of |c|, |s| keeps every scale factor within [1/sqrt2, 1]:
+        //   |c| >= |s|: new = c sc (C + k1 N),  carry = c sn (N + k2 C)
+        //   |s| >  |c|: new = s sn (N + k1 C),  carry = -s sc (C + k2 N)
+        if (fabs(c) >= fabs(s)) {
+          gr.swap[i] = 0;
+          gr.k1[i] = (T)(s * sn / (c * sc));
+          gr.k2[i] = (T)(-s * sc / (c * sn));
+          s_scale[i] = c * sc;
+          sc = c * sn;
+        } else {
+          gr.swap[i] = 1;
+          gr.k1[i] = (T)(c * sc / (s * sn));
+          gr.k2[i] = (T)(-c * sn / (s * sc));
+          s_scale[i] = s * sn;
+          sc = -s * sc;
+        }
+        if (!fast) s_scale[i] = 1.0;
       }
-      s_sc[0] = (T)st->scale[0];
     } else if (d == a.M && d == 1) {
       d = 0;   // dropping the only column leaves an empty space
     }
@@ -376,7 +453,7 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
   if (rot) {
-#define SG_CALL(D) givens_body<T, D, EN>(a, s_sc, s_c, s_s, s_cin, s_sin, v)
+#define SG_CALL(D) givens_body<T, D, EN>(a, gr, s_fast != 0, v)
     SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
   } else {
@@ -392,8 +469,8 @@ __global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
         for (int i = 0; i < SG_SMAX * SG_SMAX; ++i) st->R[i] = 0.0;
         for (int i = 0; i < d; ++i)
           for (int j = 0; j < d; ++j) st->R[i * SG_SMAX + j] = sR[i * SG_SMAX + j];
-        for (int j = 0; j < SG_SMAX; ++j) st->scale[j] = 1.0;
-        for (int j = 0; j < d; ++j) st->c1[j] = tot[j];
+        for (int j = 0; j < SG_SMAX; ++j) st->scale[j] = (j < d) ? s_scale[j] : 1.0;
+        for (int j = 0; j < d; ++j) st->c1[j] = s_scale[j] * tot[j];
       } else {
         for (int j = 0; j < d; ++j) st->c1[j] = st->scale[j] * tot[j];
       }

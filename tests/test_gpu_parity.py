@@ -237,7 +237,7 @@ def test_zero_guess(sg):
 
 
 # ---------------------------------------------------------------- projection
-def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dtype="f64"):
+def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dtype="f64", xscale=1.0):
     ref = SemOperator(*E, p, lam)
     op = sg.Op(*E, p, lam, dtype)
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -251,7 +251,7 @@ def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dt
     tolr = 1e-12 if dtype == "f64" else 2e-4
     prev = []
     for k in range(steps):
-        b = ref.apply(rng.standard_normal(ref.n) * ref.interior)
+        b = ref.apply(rng.standard_normal(ref.n) * ref.interior) * xscale
         x0 = torch.full((ref.n,), 3.0, dtype=tdt, device="cuda")
         g.form(dev(b, tdt), x0)
         want = o.form(b, np.full(ref.n, 3.0))
@@ -260,7 +260,7 @@ def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dt
             x = 0.5 * prev[-1] + 0.25 * prev[-2]
         else:
             x = (np.cos(0.3 * k) * base[0] + np.sin(0.2 * k) * base[1] + 0.1 * k * base[2]
-                 + 1e-3 * rng.standard_normal(ref.n) * ref.interior)
+                 + 1e-3 * rng.standard_normal(ref.n) * ref.interior) * xscale
         if dtype == "f32":
             x = np.float32(x).astype(np.float64)
         g.update(dev(x, tdt))
@@ -276,6 +276,19 @@ def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dt
 @pytest.mark.parametrize("M", [1, 2, 3, 5])
 def test_proj_qr_sequence(sg, M):
     _proj_sequence(sg, ProjectionQR, "qr", M)
+
+
+def test_proj_qr_long_sequence(sg):
+    """40 steps of QR(4): 36 Givens downdates in the factored form, whose
+    column scales are carried from step to step."""
+    _proj_sequence(sg, ProjectionQR, "qr", 4, steps=40)
+
+
+@pytest.mark.parametrize("method,klass", [("qr", ProjectionQR), ("energy", ProjectionEnergy)])
+def test_proj_sequence_tiny_values(sg, method, klass):
+    """Solutions of size ~1e-100 give column scales ~1e100, outside the range
+    the factored downdate keeps; the downdate then runs in the plain form."""
+    _proj_sequence(sg, klass, method, 3, xscale=1e-100)
 
 
 def test_proj_qr_sequence_f32(sg):
