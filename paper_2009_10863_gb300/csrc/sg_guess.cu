@@ -273,7 +273,7 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
                                              T (&acc)[SG_NZ(D)]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+    const int nv = n / W, stride_i = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
     V tv;
     if (DOTS) tv = reinterpret_cast<const V*>(t)[i];
@@ -287,8 +287,11 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
       const V nx = colv(base, stride, j + 1)[i];
       V o;
       if (FAST) {
-        const bool sw = gr.swap[j] != 0;
-        const T k1 = gr.k1[j], k2 = gr.k2[j];
+        // coefficients re-read from shared memory on every element: held in
+        // registers across the loop they would cost 3 per rotation
+        const bool sw = reinterpret_cast<const volatile int*>(gr.swap)[j] != 0;
+        const T k1 = reinterpret_cast<const volatile T*>(gr.k1)[j];
+        const T k2 = reinterpret_cast<const volatile T*>(gr.k2)[j];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
           const T x = sw ? vel(nx, w) : vel(carry, w);
@@ -297,7 +300,8 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
           vel(carry, w) = fma(k2, x, y);
         }
       } else {
-        const T q0 = gr.q[0][j], q1 = gr.q[1][j], q2 = gr.q[2][j], q3 = gr.q[3][j];
+        const volatile T* q = &gr.q[0][0];
+        const T q0 = q[j], q1 = q[SG_SMAX + j], q2 = q[2 * SG_SMAX + j], q3 = q[3 * SG_SMAX + j];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
           const T cv = vel(carry, w), nv_ = vel(nx, w);
@@ -374,87 +378,107 @@ __device__ __forceinline__ T vdot(const T* u, const T* t, int n) {
 // restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2
 // (energy: c1 = X~^T t = (X~, x_k)_A and ||x_k||_A^2 = x_k . t).
 template <typename T, bool EN, int DMAX>
-__global__ void __launch_bounds__(256) k_proj_upd1(const ProjArgs<T> a) {
+// 3 CTAs per SM (85 registers): the rotation sweep is bound by the loads in
+// flight, and the extra CTA beats the few spills it costs (measured: QR(8)
+// update sweeps 284 -> 267 us at 1.44M nodes)
+__global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
   __shared__ double sred[32 * NV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
   __shared__ GivensCoef<T> gr;
+  __shared__ double s_sc[SG_SMAX];      // column scales before the downdate
   __shared__ double s_scale[SG_SMAX];   // column scales after the downdate
-  __shared__ int s_d, s_rot, s_fast;
+  __shared__ double s_cr[SG_SMAX], s_sr[SG_SMAX];
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    const ProjState* st = a.st;
-    int d = st->d;
-    int rot = 0;
-    if (a.classic) {
-      if (d >= a.M) d = 0;   // hard restart: the new vector starts a fresh space
-    } else if (d == a.M && d > 1) {
-      rot = 1;
-      // R <- R(:, 2:d): a d x (d-1) upper Hessenberg matrix
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d - 1; ++j) sR[i * SG_SMAX + j] = st->R[i * SG_SMAX + j + 1];
-      // factored form while every scale stays within 2^-e..2^e (stored
-      // values then stay far from overflow and underflow in T)
-      const double lim = sizeof(T) == 8 ? 0x1p300 : 0x1p40;
-      int fast = 1;
-      for (int j = 0; j < d; ++j) {
-        const double m = fabs(st->scale[j]);
-        if (!(m < lim && m > 1.0 / lim)) fast = 0;
-      }
-      s_fast = fast;
-      gr.sc0 = (T)st->scale[0];
-      double sc = st->scale[0];   // scale of the stored carry column
+  // every thread reads the same history size (the state changes only in the
+  // last block, after all blocks have passed this point)
+  const ProjState* st = a.st;
+  int d = st->d;
+  int rot = 0;
+  if (a.classic) {
+    if (d >= a.M) d = 0;   // hard restart: the new vector starts a fresh space
+  } else if (d == a.M && d > 1) {
+    rot = 1;
+  } else if (d == a.M && d == 1) {
+    d = 0;   // dropping the only column leaves an empty space
+  }
+  bool fast = true;
+  if (rot) {
+    // R <- R(:, 2:d): a d x (d-1) upper Hessenberg matrix
+    for (int k = tid; k < d * (d - 1); k += blockDim.x) {
+      const int i = k / (d - 1), j = k - i * (d - 1);
+      sR[i * SG_SMAX + j] = st->R[i * SG_SMAX + j + 1];
+    }
+    if (tid < d) s_sc[tid] = st->scale[tid];
+    __syncthreads();
+    // factored form while every scale stays within 2^-e..2^e (stored values
+    // then stay far from overflow and underflow in T)
+    const double lim = sizeof(T) == 8 ? 0x1p300 : 0x1p40;
+    for (int j = 0; j < d; ++j) {
+      const double m = fabs(s_sc[j]);
+      if (!(m < lim && m > 1.0 / lim)) fast = false;
+    }
+    if (tid < 32) {
+      // d-1 rotations restore the triangle; lane j updates column j of the
+      // two rows a rotation touches
       for (int i = 0; i < d - 1; ++i) {
-        double av = sR[i * SG_SMAX + i], bv = sR[(i + 1) * SG_SMAX + i];
-        double r = hypot(av, bv);
-        double c = 1.0, s = 0.0;
-        if (r > 0.0) { c = fabs(av) / r; s = (av >= 0.0 ? 1.0 : -1.0) * bv / r; }
-        for (int j = i; j < d - 1; ++j) {
-          double u = sR[i * SG_SMAX + j], w = sR[(i + 1) * SG_SMAX + j];
-          sR[i * SG_SMAX + j] = c * u + s * w;
-          sR[(i + 1) * SG_SMAX + j] = -s * u + c * w;
+        const double av = sR[i * SG_SMAX + i], bv = sR[(i + 1) * SG_SMAX + i];
+        const double r = hypot(av, bv);
+        double c = 1.0, sv = 0.0;
+        if (r > 0.0) { c = fabs(av) / r; sv = (av >= 0.0 ? 1.0 : -1.0) * bv / r; }
+        __syncwarp();
+        const int j = tid;
+        if (j >= i && j < d - 1) {
+          const double u = sR[i * SG_SMAX + j], w = sR[(i + 1) * SG_SMAX + j];
+          sR[i * SG_SMAX + j] = c * u + sv * w;
+          sR[(i + 1) * SG_SMAX + j] = -sv * u + c * w;
         }
-        // new_i = c L_i + s L_{i+1}, carry = -s L_i + c L_{i+1} on the true
-        // columns L = scale * stored.  Plain form: the carry holds true
-        // values, the incoming stored column N has scale sn.
-        const double sn = st->scale[i + 1];
+        if (tid == 0) { s_cr[i] = c; s_sr[i] = sv; }
+        __syncwarp();
+      }
+      // new_i = c L_i + s L_{i+1}, carry = -s L_i + c L_{i+1} on the true
+      // columns L = scale * stored; lane i forms the coefficients of rotation i
+      const int i = tid;
+      if (i < d - 1) {
+        const double c = s_cr[i], sv = s_sr[i], sn = s_sc[i + 1];
+        // Plain form: the carry holds true values, the incoming stored
+        // column N has scale sn.
         gr.q[0][i] = (T)c;
-        gr.q[1][i] = (T)(s * sn);
-        gr.q[2][i] = (T)(-s);
+        gr.q[1][i] = (T)(sv * sn);
+        gr.q[2][i] = (T)(-sv);
         gr.q[3][i] = (T)(c * sn);
-        // Factored form: stored carry C has scale sc.  Taking out the larger
-        // of |c|, |s| keeps every scale factor within [1/sqrt2, 1]:
+        // Factored form: the stored carry C has scale sc (the chain of the
+        // rotations before this one).  Taking out the larger of |c|, |s|
+        // keeps every scale factor within [1/sqrt2, 1]:
         //   |c| >= |s|: new = c sc (C + k1 N),  carry = c sn (N + k2 C)
         //   |s| >  |c|: new = s sn (N + k1 C),  carry = -s sc (C + k2 N)
-        if (fabs(c) >= fabs(s)) {
+        double sc = s_sc[0];
+        for (int k = 0; k < i; ++k)
+          sc = fabs(s_cr[k]) >= fabs(s_sr[k]) ? s_cr[k] * s_sc[k + 1] : -s_sr[k] * sc;
+        if (fabs(c) >= fabs(sv)) {
           gr.swap[i] = 0;
-          gr.k1[i] = (T)(s * sn / (c * sc));
-          gr.k2[i] = (T)(-s * sc / (c * sn));
-          s_scale[i] = c * sc;
-          sc = c * sn;
+          gr.k1[i] = (T)(sv * sn / (c * sc));
+          gr.k2[i] = (T)(-sv * sc / (c * sn));
+          s_scale[i] = fast ? c * sc : 1.0;
         } else {
           gr.swap[i] = 1;
-          gr.k1[i] = (T)(c * sc / (s * sn));
-          gr.k2[i] = (T)(-c * sn / (s * sc));
-          s_scale[i] = s * sn;
-          sc = -s * sc;
+          gr.k1[i] = (T)(c * sc / (sv * sn));
+          gr.k2[i] = (T)(-c * sn / (sv * sc));
+          s_scale[i] = fast ? sv * sn : 1.0;
         }
-        if (!fast) s_scale[i] = 1.0;
       }
-    } else if (d == a.M && d == 1) {
-      d = 0;   // dropping the only column leaves an empty space
+      if (tid == 0) gr.sc0 = (T)s_sc[0];
     }
-    s_d = rot ? d - 1 : d;   // columns the new vector is projected on
-    s_rot = rot;
   }
-  __syncthreads();
-  const int d = s_d;
-  const int rot = s_rot;
+  if (rot) {
+    __syncthreads();
+    d -= 1;   // columns the new vector is projected on
+  }
   double v[NV], tot[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
   if (rot) {
-#define SG_CALL(D) givens_body<T, D, EN>(a, gr, s_fast != 0, v)
-    SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
+#define SG_CALL(D) givens_body<T, D, EN>(a, gr, fast, v)
+    SG_COLS_DISPATCH_UPTO(DMAX - 1, d, SG_CALL)   // d - 1 < M <= DMAX rotations
 #undef SG_CALL
   } else {
 #define SG_CALL(D) dots_body<T, D>(EN ? a.X : a.B, a.stride, a.t, a.n, v)
@@ -645,6 +669,21 @@ int reduce_blocks(int64_t n, int W) {
   return (int)(b < cap ? b : cap);
 }
 
+// Blocks for a grid-stride reduction kernel: at most one wave of resident
+// CTAs (the CTAs of a second wave would repeat the per-CTA set-up after the
+// first wave has drained), at most the reduce_blocks count the partials
+// buffer holds.
+template <typename K>
+int one_wave(K kernel, int nb, int& cached) {
+  if (cached == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    cached = per_sm * sg_num_sms();
+  }
+  return nb < cached ? nb : cached;
+}
+
 struct GuessLayout { size_t state, partials, a, b, t, slot, total; int blocks, nsl; };
 
 GuessLayout guess_layout(int64_t n, int s, int method, int dtype) {
@@ -723,9 +762,10 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
   const int nb = reduce_blocks(g->n, VecT<T>::W);
   {
     ProfScope ps(PROF_PROJ_DOTS, s);
-    if (g->s <= 4) k_proj_dots<T, 4><<<nb, 256, 0, s>>>(a);
-    else if (g->s <= 8) k_proj_dots<T, 8><<<nb, 256, 0, s>>>(a);
-    else k_proj_dots<T, 16><<<nb, 256, 0, s>>>(a);
+    static int w4 = 0, w8 = 0, w16 = 0;
+    if (g->s <= 4) k_proj_dots<T, 4><<<one_wave(k_proj_dots<T, 4>, nb, w4), 256, 0, s>>>(a);
+    else if (g->s <= 8) k_proj_dots<T, 8><<<one_wave(k_proj_dots<T, 8>, nb, w8), 256, 0, s>>>(a);
+    else k_proj_dots<T, 16><<<one_wave(k_proj_dots<T, 16>, nb, w16), 256, 0, s>>>(a);
     SG_LAUNCH_CHECK("k_proj_dots");
   }
   {
@@ -740,11 +780,12 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
 
 template <typename T, bool EN, int DMAX>
 int proj_update_sweeps(const ProjArgs<T>& a, int nb, cudaStream_t s) {
-  k_proj_upd1<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  static int w1 = 0, w2 = 0, w3 = 0;
+  k_proj_upd1<T, EN, DMAX><<<one_wave(k_proj_upd1<T, EN, DMAX>, nb, w1), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd1");
-  k_proj_upd2<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  k_proj_upd2<T, EN, DMAX><<<one_wave(k_proj_upd2<T, EN, DMAX>, nb, w2), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd2");
-  k_proj_upd3<T, EN, DMAX><<<nb, 256, 0, s>>>(a);
+  k_proj_upd3<T, EN, DMAX><<<one_wave(k_proj_upd3<T, EN, DMAX>, nb, w3), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd3");
   return SG_OK;
 }
