@@ -97,8 +97,13 @@ struct __align__(16) EOTab {
 };
 
 // o[0..P] = C u for one element line (even-odd), coefficients from table t.
-template <typename T, int P>
-__device__ __forceinline__ void line_eo(const T (&u)[P + 1], const EOTab<T, P>& t, T (&o)[P + 1]) {
+// With ROW, o[0] also receives row p of C applied to the line ul of the
+// element before (the other element of the shared node 0).
+// Per output pair the odd sum starts from the even one, op = E_a + O_a, and
+// o[p-a] = 2 E_a - op: one multiply-add instead of a multiply and two adds.
+template <typename T, int P, bool ROW>
+__device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1], const EOTab<T, P>& t,
+                                        T (&o)[P + 1]) {
   using TL = SemTile<P>;
   constexpr int H = TL::H;
   T s[H], d[H];
@@ -107,17 +112,23 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const EOTab<T, P>& 
 #pragma unroll
   for (int a = 0; a < H; ++a) {
     T e = t.ce[a][0] * s[0];
-    T od = t.co[a][0] * d[0];
 #pragma unroll
-    for (int l = 1; l < H; ++l) { e += t.ce[a][l] * s[l]; od += t.co[a][l] * d[l]; }
-    if (TL::MID) e += t.cm[a] * u[P / 2];
-    o[a] = e + od;
-    o[P - a] = e - od;
+    for (int l = 1; l < H; ++l) e = fma(t.ce[a][l], s[l], e);
+    if (TL::MID) e = fma(t.cm[a], u[P / 2], e);
+    T op = e;
+#pragma unroll
+    for (int l = 0; l < H; ++l) op = fma(t.co[a][l], d[l], op);
+    o[P - a] = fma((T)2, e, -op);
+    if (ROW && a == 0) {
+#pragma unroll
+      for (int l = 0; l <= P; ++l) op = fma(t.crow[l], ul[l], op);
+    }
+    o[a] = op;
   }
   if (TL::MID) {
     T e = t.cm[H] * u[P / 2];
 #pragma unroll
-    for (int l = 0; l < H; ++l) e += t.ce[H][l] * s[l];
+    for (int l = 0; l < H; ++l) e = fma(t.ce[H][l], s[l], e);
     o[P / 2] = e;
   }
 }
@@ -194,11 +205,24 @@ template <typename T, int P, bool CREG>
 __device__ __forceinline__ void dir_line(const T (&u)[P + 1], T (&o)[P + 1], const EOTab<T, P>& st,
                                          const EOTab<T, P>& rt, T scale) {
   if constexpr (CREG) {
-    line_eo<T, P>(u, rt, o);
+    line_eo<T, P, false>(u, u, rt, o);
 #pragma unroll
     for (int c = 0; c <= P; ++c) o[c] *= scale;
   } else {
-    line_eo<T, P>(u, st, o);
+    line_eo<T, P, false>(u, u, st, o);
+  }
+}
+
+// The same with row p of C on the element before added to o[0] (x and y lines).
+template <typename T, int P, bool CREG>
+__device__ __forceinline__ void dir_line_row(const T (&u)[P + 1], const T (&ul)[P + 1], T (&o)[P + 1],
+                                             const EOTab<T, P>& st, const EOTab<T, P>& rt, T scale) {
+  if constexpr (CREG) {
+    line_eo<T, P, true>(u, ul, rt, o);
+#pragma unroll
+    for (int c = 0; c <= P; ++c) o[c] *= scale;
+  } else {
+    line_eo<T, P, true>(u, ul, st, o);
   }
 }
 
@@ -349,8 +373,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
-      dir_line<T, P, CREG>(ue, o, sTab[0], rt, sx);
-      o[0] += dir_row<T, P, CREG>(ul, sTab[0], rt, sx);
+      dir_line_row<T, P, CREG>(ue, ul, o, sTab[0], rt, sx);
       T* w = Wb + ((size_t)xi_c * TY + xi_r) * TX + xi_e * P;
 #pragma unroll
       for (int c = 0; c < P; ++c) w[c] = o[c];
@@ -378,8 +401,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
-      dir_line<T, P, CREG>(ue, o, sTab[1], rt, sy);
-      o[0] += dir_row<T, P, CREG>(ul, sTab[1], rt, sy);
+      dir_line_row<T, P, CREG>(ue, ul, o, sTab[1], rt, sy);
       T* w = Wy + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
       if constexpr (TWO_W) {
 #pragma unroll
