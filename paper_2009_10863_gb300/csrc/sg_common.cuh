@@ -84,6 +84,7 @@ struct SemGeom {
   double C[3][SG_PMAX + 1][SG_PMAX + 1];  // per direction x, y, z
   double wl[SG_PMAX + 1];  // assembled 1D mass by local index (wl[0] = w0 + wp)
   double dg[3][SG_PMAX + 1];              // diagonal coefficient by local index
+  const void* tabs;        // device: the operator kernel's weighted even-odd tables (sg_op.cu)
 };
 
 struct sg_op_s {
@@ -97,6 +98,7 @@ struct sg_op_s {
   unsigned long long uid;   // unique per created operator (never reused)
   int last_iters;           // iterations of the last PCG solve (sizes the first chunk)
   void* pcg_graphs;         // cached PCG iteration graphs (sg_pcg.cu), released with the operator
+  void* d_tabs;             // device copy of the operator kernel's tables (g.tabs)
 };
 
 // Release the PCG iteration graphs cached on an operator (sg_pcg.cu).

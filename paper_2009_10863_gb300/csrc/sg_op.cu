@@ -140,6 +140,55 @@ static void build_geom(sg_op_s* op) {
   g.cm = op->lambda * hx * hy * hz / 8.0;
 }
 
+// The operator kernel's 2p+1 weighted even-odd tables (sem_tables), built in
+// FP64 on the host, rounded to the operator's dtype and copied to the device
+// once; every CTA copies them into shared memory.
+template <typename T, int P>
+static void fill_tables(const SemGeom& g, std::vector<unsigned char>& buf) {
+  buf.assign(sizeof(EOTab<T, P>) * sem_ntabs<P>(), 0);
+  sem_tables<T, P>(g, reinterpret_cast<EOTab<T, P>*>(buf.data()));
+}
+
+template <typename T>
+static void fill_tables_p(const SemGeom& g, std::vector<unsigned char>& buf) {
+  switch (g.p) {
+    case 1: fill_tables<T, 1>(g, buf); break;
+    case 2: fill_tables<T, 2>(g, buf); break;
+    case 3: fill_tables<T, 3>(g, buf); break;
+    case 4: fill_tables<T, 4>(g, buf); break;
+    case 5: fill_tables<T, 5>(g, buf); break;
+    case 6: fill_tables<T, 6>(g, buf); break;
+    case 7: fill_tables<T, 7>(g, buf); break;
+    default: fill_tables<T, 8>(g, buf); break;
+  }
+}
+
+static int upload_tables(sg_op_s* op) {
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    // a host without a CUDA device: nothing can be launched, the handle still
+    // answers the host queries (size, GLL nodes); launches refuse it
+    cudaGetLastError();
+    return SG_OK;
+  }
+  std::vector<unsigned char> buf;
+  if (op->dtype == SG_F64) fill_tables_p<double>(op->g, buf);
+  else fill_tables_p<float>(op->g, buf);
+  cudaError_t e = cudaMalloc(&op->d_tabs, buf.size());
+  if (e != cudaSuccess) {
+    op->d_tabs = nullptr;
+    return sg_fail(SG_ERR_CUDA, std::string("op_create: table allocation: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(op->d_tabs, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(op->d_tabs);
+    op->d_tabs = nullptr;
+    return sg_fail(SG_ERR_CUDA, std::string("op_create: table upload: ") + cudaGetErrorString(e));
+  }
+  op->g.tabs = op->d_tabs;
+  return SG_OK;
+}
+
 extern "C" int sg_op_create(sg_op_t* out, int ex, int ey, int ez, int p, double lambda, int dtype) {
   if (!out) return sg_fail(SG_ERR_INVALID, "op_create: NULL output handle");
   *out = nullptr;
@@ -168,6 +217,10 @@ extern "C" int sg_op_create(sg_op_t* out, int ex, int ey, int ez, int p, double 
     }
   }
   cudaGetDevice(&op->device);
+  if (int rc = upload_tables(op)) {
+    delete op;
+    return rc;
+  }
   static std::atomic<unsigned long long> next_uid{1};
   op->uid = next_uid.fetch_add(1);
   *out = op;
@@ -175,7 +228,10 @@ extern "C" int sg_op_create(sg_op_t* out, int ex, int ey, int ez, int p, double 
 }
 
 extern "C" int sg_op_destroy(sg_op_t op) {
-  if (op) sg_pcg_release(op);
+  if (op) {
+    sg_pcg_release(op);
+    if (op->d_tabs) cudaFree(op->d_tabs);
+  }
   delete op;
   return SG_OK;
 }

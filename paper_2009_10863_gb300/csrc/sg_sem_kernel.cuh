@@ -86,15 +86,26 @@ struct SemArgs {
   int final_pass; // MODE 2: 1 = true-residual check (store rr_true only)
 };
 
-// Even-odd coefficient tables of one direction (scaled by the direction factor).
+// Even-odd coefficient tables of one direction's C, rows multiplied by the
+// assembled mass weights of the output nodes (see sem_tables).
 template <typename T, int P>
 struct __align__(16) EOTab {
   using TL = SemTile<P>;
-  T ce[TL::HE][TL::H];   // (C[a][l] + C[a][p-l]) / 2, a < H (+ middle row)
-  T co[TL::H][TL::H];    // (C[a][l] - C[a][p-l]) / 2, a < H
-  T cm[TL::HE];          // C[a][mid] (odd line length only)
-  T crow[P + 1];         // row p of C: contribution to the next element's node 0
+  T ce[TL::HE][TL::H];            // (C[a][l] + C[a][p-l]) / 2, a < H (+ middle row)
+  T co[TL::H][TL::H];             // (C[a][l] - C[a][p-l]) / 2, a < H
+  T cm[TL::MID ? TL::HE : 1];     // C[a][mid] (odd line length only)
+  T crow[P + 1];                  // row p of C: contribution to the next element's node 0
 };
+
+// The 2p+1 tables a CTA uses, built once per operator on the host (sg_op.cu)
+// and copied into shared memory by every CTA:
+//   [0]        z: C_z + c_m I, row a multiplied by W_a (W_p = W_0)
+//   [1 + c]    x, for output plane c (local z index c < p): W_c C_x
+//   [1 + p + c] y, for output plane c: W_c C_y
+// so that every line product already carries the z weight W_k of its output
+// nodes and the epilogue multiplies by W_i W_j only.
+template <int P>
+constexpr int sem_ntabs() { return 2 * P + 1; }
 
 // o[0..P] = C u for one element line (even-odd), coefficients from table t.
 // With ROW, o[0] also receives row p of C applied to the line ul of the
@@ -114,7 +125,7 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1
     T e = t.ce[a][0] * s[0];
 #pragma unroll
     for (int l = 1; l < H; ++l) e = fma(t.ce[a][l], s[l], e);
-    if (TL::MID) e = fma(t.cm[a], u[P / 2], e);
+    if constexpr (TL::MID) e = fma(t.cm[a], u[P / 2], e);
     T op = e;
 #pragma unroll
     for (int l = 0; l < H; ++l) op = fma(t.co[a][l], d[l], op);
@@ -125,7 +136,7 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1
     }
     o[a] = op;
   }
-  if (TL::MID) {
+  if constexpr (TL::MID) {
     T e = t.cm[H] * u[P / 2];
 #pragma unroll
     for (int l = 0; l < H; ++l) e = fma(t.ce[H][l], s[l], e);
@@ -141,95 +152,45 @@ __device__ __forceinline__ T row_dot(const T (&u)[P + 1], const EOTab<T, P>& t) 
   return r;
 }
 
-// Tables of direction d, multiplied by ``mul`` (1 for the scaled tables; 1/a_d
-// for an unscaled copy).  ``dadd`` is added to the diagonal of C before the
-// split (the z tables carry the mass term c_m this way): rows 1..p-1 get dadd,
-// the shared rows 0 and p get dadd/2 each, so a shared node, which sums row 0
-// of its element and row p of the element below, gets dadd once.  The sum
-// keeps C centrosymmetric.
+// Table of direction d with row a of C multiplied by rowmul[a] (rowmul[p] =
+// rowmul[0] keeps C centrosymmetric).  ``dadd`` is added to the diagonal of C
+// before the split (the z table carries the mass term c_m this way): rows
+// 1..p-1 get dadd, the shared rows 0 and p get dadd/2 each, so a shared node,
+// which sums row 0 of its element and row p of the element below, gets dadd
+// once.
 template <typename T, int P>
-__host__ __device__ inline void build_eotab(const SemGeom& g, int d, double mul, EOTab<T, P>& t, double dadd = 0.0) {
+inline void build_eotab(const SemGeom& g, int d, const double (&rowmul)[P + 1], EOTab<T, P>& t,
+                        double dadd = 0.0) {
   using TL = SemTile<P>;
   constexpr int H = TL::H;
   double Cm[P + 1][P + 1];
   for (int a = 0; a <= P; ++a)
     for (int l = 0; l <= P; ++l)
-      Cm[a][l] = g.C[d][a][l] + ((a == l) ? ((a == 0 || a == P) ? 0.5 * dadd : dadd) : 0.0);
+      Cm[a][l] = rowmul[a] * (g.C[d][a][l] + ((a == l) ? ((a == 0 || a == P) ? 0.5 * dadd : dadd) : 0.0));
   for (int a = 0; a < TL::HE; ++a) {
     const int aa = (a < H) ? a : P / 2;
     for (int l = 0; l < H; ++l) {
-      t.ce[a][l] = (T)(mul * 0.5 * (Cm[aa][l] + Cm[aa][P - l]));
-      if (a < H) t.co[a][l] = (T)(mul * 0.5 * (Cm[aa][l] - Cm[aa][P - l]));
+      t.ce[a][l] = (T)(0.5 * (Cm[aa][l] + Cm[aa][P - l]));
+      if (a < H) t.co[a][l] = (T)(0.5 * (Cm[aa][l] - Cm[aa][P - l]));
     }
-    t.cm[a] = TL::MID ? (T)(mul * Cm[aa][P / 2]) : (T)0;
+    if constexpr (TL::MID) t.cm[a] = (T)Cm[aa][P / 2];
   }
-  for (int l = 0; l <= P; ++l) t.crow[l] = (T)(mul * Cm[P][l]);
+  if constexpr (!TL::MID) t.cm[0] = (T)0;
+  for (int l = 0; l <= P; ++l) t.crow[l] = (T)Cm[P][l];
 }
 
-// The tables of all three directions (build_eotab with mul = 1, the mass term
-// c_m added to z), each entry computed by its own thread: a CTA's set-up costs
-// a few FP64 operations per thread instead of the whole table on one thread.
+// The 2p+1 tables of sem_ntabs (host).
 template <typename T, int P>
-__device__ __forceinline__ void build_eotabs_par(const SemGeom& g, EOTab<T, P>* tabs, int tid, int nthreads) {
-  using TL = SemTile<P>;
-  constexpr int H = TL::H, HE = TL::HE;
-  constexpr int NCE = HE * H, NCO = H * H, NCM = HE, NCR = P + 1;
-  constexpr int PER = NCE + NCO + NCM + NCR;
-  for (int q = tid; q < 3 * PER; q += nthreads) {
-    const int d = q / PER;
-    int r = q - d * PER;
-    const double dadd = (d == 2) ? g.cm : 0.0;
-    auto Cm = [&](int a, int l) {
-      return g.C[d][a][l] + ((a == l) ? ((a == 0 || a == P) ? 0.5 * dadd : dadd) : 0.0);
-    };
-    EOTab<T, P>& t = tabs[d];
-    if (r < NCE) {
-      const int a = r / H, l = r - (r / H) * H, aa = (a < H) ? a : P / 2;
-      t.ce[a][l] = (T)(0.5 * (Cm(aa, l) + Cm(aa, P - l)));
-    } else if ((r -= NCE) < NCO) {
-      const int a = r / H, l = r - (r / H) * H;
-      t.co[a][l] = (T)(0.5 * (Cm(a, l) - Cm(a, P - l)));
-    } else if ((r -= NCO) < NCM) {
-      const int aa = (r < H) ? r : P / 2;
-      t.cm[r] = TL::MID ? (T)Cm(aa, P / 2) : (T)0;
-    } else {
-      r -= NCM;
-      t.crow[r] = (T)Cm(P, r);
-    }
+inline void sem_tables(const SemGeom& g, EOTab<T, P>* tabs) {
+  double wz[P + 1], wc[P + 1];
+  for (int a = 0; a < P; ++a) wz[a] = g.wl[a];
+  wz[P] = g.wl[0];
+  build_eotab<T, P>(g, 2, wz, tabs[0], g.cm);
+  for (int c = 0; c < P; ++c) {
+    for (int a = 0; a <= P; ++a) wc[a] = g.wl[c];
+    build_eotab<T, P>(g, 0, wc, tabs[1 + c]);
+    build_eotab<T, P>(g, 1, wc, tabs[1 + P + c]);
   }
-}
-
-// One direction's line product: FP64 reads the scaled table of the direction
-// from shared memory; FP32 uses the unscaled register table times a_d.
-template <typename T, int P, bool CREG>
-__device__ __forceinline__ void dir_line(const T (&u)[P + 1], T (&o)[P + 1], const EOTab<T, P>& st,
-                                         const EOTab<T, P>& rt, T scale) {
-  if constexpr (CREG) {
-    line_eo<T, P, false>(u, u, rt, o);
-#pragma unroll
-    for (int c = 0; c <= P; ++c) o[c] *= scale;
-  } else {
-    line_eo<T, P, false>(u, u, st, o);
-  }
-}
-
-// The same with row p of C on the element before added to o[0] (x and y lines).
-template <typename T, int P, bool CREG>
-__device__ __forceinline__ void dir_line_row(const T (&u)[P + 1], const T (&ul)[P + 1], T (&o)[P + 1],
-                                             const EOTab<T, P>& st, const EOTab<T, P>& rt, T scale) {
-  if constexpr (CREG) {
-    line_eo<T, P, true>(u, ul, rt, o);
-#pragma unroll
-    for (int c = 0; c <= P; ++c) o[c] *= scale;
-  } else {
-    line_eo<T, P, true>(u, ul, st, o);
-  }
-}
-
-template <typename T, int P, bool CREG>
-__device__ __forceinline__ T dir_row(const T (&u)[P + 1], const EOTab<T, P>& st, const EOTab<T, P>& rt, T scale) {
-  if constexpr (CREG) return scale * row_dot<T, P>(u, rt);
-  else return row_dot<T, P>(u, st);
 }
 
 // cp.async of one element, zero-filled when !valid (nothing is read then).
@@ -262,20 +223,23 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
   constexpr int PLANE = PX * PY;
   constexpr int K = (PLANE + NT - 1) / NT;       // staged elements per thread per plane
-  constexpr bool CREG = false;                    // coefficients read from shared memory (broadcast)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);         // NPL ring slots of PY x PX
   constexpr bool TWO_W = TL::template two_w<T>();
   T* Wb = S + (size_t)NPL * PLANE;               // P planes of TY x TX (x results)
   T* Wy = TWO_W ? Wb + (size_t)P * TY * TX : Wb; // y results (same buffer for FP64)
-  __shared__ EOTab<T, P> sTab[4];
+  __shared__ EOTab<T, P> sTab[sem_ntabs<P>()];
   __shared__ T sW[P + 1];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
   if (lead_sync) __syncthreads();                // shared memory of a previous item is free
-  build_eotabs_par<T, P>(g, sTab, tid, NT);     // x, y, z tables (mass term in z), one entry per thread
-  if (CREG && tid == 3) build_eotab<T, P>(g, 0, 1.0 / g.adir[0], sTab[3]);
+  {                                              // the operator's tables (L2-resident), copied
+    constexpr int NW = sem_ntabs<P>() * (int)(sizeof(EOTab<T, P>) / sizeof(T));
+    const T* src = static_cast<const T*>(g.tabs);
+    T* dst = reinterpret_cast<T*>(sTab);
+    for (int i = tid; i < NW; i += NT) dst[i] = __ldg(src + i);
+  }
   if (tid <= P) sW[tid] = (T)g.wl[tid];
   __syncthreads();
   if (skip_s && *skip_s) return;
@@ -305,9 +269,6 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     }
   };
 
-  EOTab<T, P> rt;                 // FP32: register copy of the unscaled table
-  if constexpr (CREG) rt = sTab[3];
-  const T sx = (T)g.adir[0], sy = (T)g.adir[1], sz = (T)g.adir[2];
 
   const int gx = x0 + tx, gy = y0 + ty;
   const int ia = tx % P, ib = ty % P;
@@ -331,7 +292,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       const int gz = (e0 - 1) * P + l;
       ub[l] = (gz > 0) ? a.x[(size_t)gx + (size_t)g.nx * gy + nxy * gz] : (T)0;
     }
-    carry = dir_row<T, P, CREG>(ub, sTab[2], rt, sz);
+    carry = row_dot<T, P>(ub, sTab[0]);
   }
 
   // x / y item coordinates (one item per thread per phase)
@@ -360,7 +321,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       u[l] = S[slot_of(l) * PLANE + (ty + P) * PX + (tx + P)];
     {
       T o[P + 1];
-      dir_line<T, P, CREG>(u, o, sTab[2], rt, sz);
+      line_eo<T, P, false>(u, u, sTab[0], o);
 #pragma unroll
       for (int c = 0; c < P; ++c) acc[c] = o[c];   // includes c_m u (folded into the z tables)
       acc[0] += carry;
@@ -373,7 +334,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
-      dir_line_row<T, P, CREG>(ue, ul, o, sTab[0], rt, sx);
+      line_eo<T, P, true>(ue, ul, sTab[1 + xi_c], o);
       T* w = Wb + ((size_t)xi_c * TY + xi_r) * TX + xi_e * P;
 #pragma unroll
       for (int c = 0; c < P; ++c) w[c] = o[c];
@@ -401,7 +362,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
-      dir_line_row<T, P, CREG>(ue, ul, o, sTab[1], rt, sy);
+      line_eo<T, P, true>(ue, ul, sTab[1 + P + yi_c], o);
       T* w = Wy + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
       if constexpr (TWO_W) {
 #pragma unroll
@@ -423,7 +384,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       const int gz = e * P + c;
       const T v = acc[c] + Wy[((size_t)c * TY + ty) * TX + tx];
       const bool inside = col_int && gz > 0;
-      const T yv = inside ? (wxy * sW[c]) * v : (T)0;
+      const T yv = inside ? wxy * v : (T)0;   // W_k is in the tables
       if (col_in) {
         const size_t idx = lidx + nxy * (size_t)c;
         if (MODE == 0) {

@@ -29,6 +29,7 @@ int sg_sem_attr_p() {
 template <typename T, int P, int MODE>
 int sg_sem_launch_p(const SemGeom& g, const SemArgs<T>& a0, cudaStream_t s, int zl_override) {
   using TL = SemTile<P>;
+  if (!g.tabs) return sg_fail(SG_ERR_STATE, "sem: the operator was created without a CUDA device");
   SemArgs<T> a = a0;
   a.zl = sg_sem_layers(g, TL::TEX, TL::TEY, zl_override);
   dim3 block(TL::TX, TL::TY, 1);
