@@ -283,6 +283,25 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     cp_async_commit();
   }
 
+  // FP64 PCG step over a single element layer: the p ring slots that no
+  // later layer needs take this layer's old q and p of the owned nodes (slot
+  // of plane c: q at [tid], p at [NT + tid]), copied asynchronously while the
+  // line products run (the FP32 kernel prefetches them into registers).
+  constexpr bool PREF = sizeof(T) == 4;          // FP64: registers are too tight
+  constexpr bool SPF_FITS = 2 * NT <= PLANE;     // a slot holds one plane's q and p
+  const bool spf = SPF_FITS && !PREF && MODE == 1 && e1 == e0 + 1 && !*first_s;
+  auto pq_slot = [&](int c) { return (e0 * P + P + 1 + c) % NPL; };
+  if (spf) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      const size_t idx = colbase + nxy * (size_t)(e0 * P + c);
+      T* sl = S + (size_t)pq_slot(c) * PLANE;
+      cp_async_elem(sl + tid, a.out + (col_in ? idx : 0), col_in);
+      cp_async_elem(sl + NT + tid, a.out2 + (col_in ? idx : 0), col_in);
+    }
+    cp_async_commit();
+  }
+
   // z-carry from the element layer below the chunk (row p on its line)
   T carry = (T)0;
   if (e0 > 0 && col_int) {
@@ -305,6 +324,8 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       for (int pl = 1; pl <= P; ++pl) stage_plane((e + 1) * P + pl);
       cp_async_commit();
       cp_async_wait<1>();
+    } else if (spf) {
+      cp_async_wait<1>();                        // the planes; q and p may still be in flight
     } else {
       cp_async_wait<0>();
     }
@@ -344,7 +365,6 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     // epilogue operands of this layer's owned nodes, loaded before the y
     // contraction to overlap their latency with it
     const size_t lidx = colbase + nxy * (size_t)(e * P);
-    constexpr bool PREF = sizeof(T) == 4;        // FP64: registers are too tight
     T ea[P], eb[P];
     if (PREF && (MODE == 1 || MODE == 2)) {
 #pragma unroll
@@ -379,6 +399,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     }
 
     // ---- combine, weights, epilogue
+    if (spf) cp_async_wait<0>();                 // this thread's own q and p copies
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
@@ -393,8 +414,9 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
           T qv = yv, pv = u[c];
           if (!*first_s) {
             const T beta = *beta_s;
-            qv += beta * (PREF ? ea[c] : a.out[idx]);
-            pv += beta * (PREF ? eb[c] : a.out2[idx]);
+            const T* sl = S + (size_t)pq_slot(c) * PLANE;
+            qv += beta * (PREF ? ea[c] : (spf ? sl[tid] : a.out[idx]));
+            pv += beta * (PREF ? eb[c] : (spf ? sl[NT + tid] : a.out2[idx]));
           }
           a.out[idx] = qv;
           a.out2[idx] = pv;

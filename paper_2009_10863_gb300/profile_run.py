@@ -44,9 +44,12 @@ def main():
         op.apply(x, out=y)
     b = op.apply(x)
     xs = op.zeros()
+    sg.profile_reset()
     sg.profile_enable(True)      # host-launched iterations: each kernel is a separate launch
     it, _ = op.pcg(b, xs, 1e-10, maxit=args.pcg_iters)
     sg.profile_enable(False)
+    t_apply, n_apply = sg.profile_read(sg.PROF_PCG_APPLY)
+    t_upd, n_upd = sg.profile_read(sg.PROF_PCG_UPDATE)
     g = sg.Guess(op.n, args.s, "extrap", m=2, dtype=args.dtype)
     q = sg.Guess(op.n, args.s, "qr", eps_rel=1e-6, op=op, dtype=args.dtype)
     for k in range(args.s + 1):          # independent vectors: the QR history fills to d = s
@@ -63,8 +66,9 @@ def main():
         op.apply(x, out=y)
     e1.record()
     torch.cuda.synchronize()
-    print("nodes %d dtype %s apply %.1f us, pcg iterations %d, qr d=%d" %
-          (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, q.info()[0]))
+    print("nodes %d dtype %s apply %.1f us, pcg iterations %d (step %.1f us, update %.1f us), qr d=%d" %
+          (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, 1e3 * t_apply / max(n_apply, 1),
+           1e3 * t_upd / max(n_upd, 1), q.info()[0]))
 
 
 def sequence_steps(steps):
