@@ -32,7 +32,8 @@ struct PcgLayout {
 // is FP64 instructions, and each block's r.r / r.z reduction adds FP64 work in
 // proportion to the block count (8 CTAs per SM: 1.2 additions per node on the
 // 16^3 p = 7 mesh, 2 per SM: 0.3; measured 3.32 -> 3.72 TB/s there).  FP32
-// (vec 4): 8 per SM, a full wave, for memory-level parallelism.
+// (vec 4): 8 per SM, a full wave, for memory-level parallelism.  (FP64 with
+// 3, 4, 6 CTAs per SM measured 23.8, 24.4, 27.4 us against 23.6 us.)
 int update_blocks(int64_t n, int vec) {
   int64_t nv = (n + vec - 1) / vec;
   int64_t b = (nv + 255) / 256;
@@ -173,19 +174,41 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   T rr = 0, rz = 0;
   const int nv = n / W;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    V xv = reinterpret_cast<V*>(x)[i];
-    V pv = reinterpret_cast<const V*>(p)[i];
-    V rv = reinterpret_cast<V*>(r)[i];
-    V qv = reinterpret_cast<const V*>(q)[i];
-    V dv = reinterpret_cast<const V*>(invd)[i];
-    V zv;
+  auto step = [&](V& xv, const V& pv, V& rv, const V& qv, const V& dv, V& zv) {
     upd1(xv.x, pv.x, rv.x, qv.x, dv.x, zv.x, al, rr, rz);
     upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, rr, rz);
     if constexpr (W == 4) {
       upd1(xv.z, pv.z, rv.z, qv.z, dv.z, zv.z, al, rr, rz);
       upd1(xv.w, pv.w, rv.w, qv.w, dv.w, zv.w, al, rr, rz);
     }
+  };
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // FP64: two grid-stride elements per pass, so that both elements' ten loads
+  // are in flight together (2 CTAs per SM, see update_blocks); FP32 runs a
+  // full wave and keeps its registers for occupancy
+  for (; W == 2 && i + stride < nv; i += 2 * stride) {
+    const int j = i + stride;
+    V xa = reinterpret_cast<V*>(x)[i], xb = reinterpret_cast<V*>(x)[j];
+    const V pa = reinterpret_cast<const V*>(p)[i], pb = reinterpret_cast<const V*>(p)[j];
+    V ra = reinterpret_cast<V*>(r)[i], rb = reinterpret_cast<V*>(r)[j];
+    const V qa = reinterpret_cast<const V*>(q)[i], qb = reinterpret_cast<const V*>(q)[j];
+    const V da = reinterpret_cast<const V*>(invd)[i], db = reinterpret_cast<const V*>(invd)[j];
+    V za, zb;
+    step(xa, pa, ra, qa, da, za);
+    step(xb, pb, rb, qb, db, zb);
+    reinterpret_cast<V*>(x)[i] = xa;
+    reinterpret_cast<V*>(r)[i] = ra;
+    reinterpret_cast<V*>(z)[i] = za;
+    reinterpret_cast<V*>(x)[j] = xb;
+    reinterpret_cast<V*>(r)[j] = rb;
+    reinterpret_cast<V*>(z)[j] = zb;
+  }
+  for (; i < nv; i += stride) {
+    V xv = reinterpret_cast<V*>(x)[i];
+    V rv = reinterpret_cast<V*>(r)[i];
+    V zv;
+    step(xv, reinterpret_cast<const V*>(p)[i], rv, reinterpret_cast<const V*>(q)[i],
+         reinterpret_cast<const V*>(invd)[i], zv);
     reinterpret_cast<V*>(x)[i] = xv;
     reinterpret_cast<V*>(r)[i] = rv;
     reinterpret_cast<V*>(z)[i] = zv;
