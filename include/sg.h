@@ -100,8 +100,17 @@ const char* sg_last_error(void);
 
 /* Create an operator.  1 <= p <= SG_MAX_DEGREE, ex,ey,ez >= 1, lambda >= 0,
  * dtype SG_F64 or SG_F32 (arithmetic and storage type of sg_sem_apply and
- * sg_pcg_solve).  Allocates < 4 KB of device tables on the current device. */
+ * sg_pcg_solve).  Allocates < 8 KB of device tables (the operator kernel's
+ * coefficients) on the current device.  On a host without a CUDA device it
+ * allocates nothing; the handle then answers sg_op_size and sg_op_gll, and
+ * every launch through it returns SG_ERR_STATE. */
 int sg_op_create(sg_op_t* op, int ex, int ey, int ez, int p, double lambda, int dtype);
+/* Element layers in z that one CTA of the operator kernel marches through
+ * (a tuning and testing knob of the tiled operator of Sec. 5.1): zl >= 1
+ * fixes it (clamped to ez), 0 restores the automatic choice (about 8 CTAs per
+ * SM).  Results agree to rounding for every zl.  Drops the PCG graphs cached
+ * on the operator.  SG_ERR_INVALID for a NULL handle or zl < 0. */
+int sg_op_set_layers(sg_op_t op, int zl);
 int sg_op_destroy(sg_op_t op);
 /* n = (p*ex+1)(p*ey+1)(p*ez+1); returns -1 for a NULL handle. */
 int64_t sg_op_size(sg_op_t op);

@@ -38,6 +38,7 @@ SIGNATURES = [
     ("sg_op_destroy", _I, [_VP]),
     ("sg_op_size", _I64, [_VP]),
     ("sg_op_gll", _I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("sg_op_set_layers", _I, [_VP, _I]),
     ("sg_sem_apply", _I, [_VP, _VP, _VP, _VP]),
     ("sg_op_diagonal", _I, [_VP, _VP, _VP]),
     ("sg_pcg_workspace_bytes", _SZ, [_VP]),
@@ -153,6 +154,10 @@ class Op:
         if getattr(self, "h", None) and _lib is not None:
             _lib.sg_op_destroy(self.h)
             self.h = None
+
+    def set_layers(self, zl):
+        """Element layers per CTA of the operator kernel (0 = automatic)."""
+        _check(lib().sg_op_set_layers(self.h, int(zl)))
 
     def gll(self):
         x = (ctypes.c_double * (self.p + 1))()

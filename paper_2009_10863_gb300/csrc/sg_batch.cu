@@ -383,7 +383,11 @@ BLayout blayout(int nseq, const sg_op_t* ops) {
   L.max_blocks = 16 * sg_num_sms();
   size_t off = 0;
   L.state = off; off += align_up(sizeof(PcgState) * SG_BATCH_MAX);
-  L.partials = off; off += align_up(sizeof(double) * 3 * SG_BATCH_MAX * (size_t)(L.max_blocks > 4096 ? L.max_blocks : 4096));
+  // per-block partials of the persistent kernel and of the FP64 residual
+  // launches, whose CTA count is at most the one-layer tile count (items)
+  size_t pb = (size_t)(L.max_blocks > 4096 ? L.max_blocks : 4096);
+  if ((size_t)items > pb) pb = (size_t)items;
+  L.partials = off; off += align_up(sizeof(double) * 3 * SG_BATCH_MAX * pb);
   L.bar = off; off += align_up(sizeof(unsigned int) * 4 + sizeof(int) * 4);
   L.items = off; off += align_up(sizeof(int4) * (size_t)items);
   L.counters = off; off += align_up(sizeof(unsigned int) * SG_BATCH_MAX);

@@ -85,6 +85,7 @@ struct SemGeom {
   double wl[SG_PMAX + 1];  // assembled 1D mass by local index (wl[0] = w0 + wp)
   double dg[3][SG_PMAX + 1];              // diagonal coefficient by local index
   const void* tabs;        // device: the operator kernel's weighted even-odd tables (sg_op.cu)
+  int zl;                  // element layers per operator CTA; 0 = automatic
 };
 
 struct sg_op_s {

@@ -101,6 +101,7 @@ extern "C" int sg_profile_read(int id, double* total_ms, long long* launches) {
 
 // ---------------------------------------------------------------- operator
 int sg_sem_layers(const SemGeom& g, int tex, int tey, int override_zl) {
+  if (override_zl <= 0) override_zl = g.zl;
   if (override_zl > 0) return override_zl < g.ez ? override_zl : g.ez;
   const long nxy = (long)((g.ex + tex - 1) / tex) * ((g.ey + tey - 1) / tey);
   const long want = 8L * sg_num_sms();           // CTAs to aim for (several waves)
@@ -237,6 +238,14 @@ extern "C" int sg_op_destroy(sg_op_t op) {
 }
 
 extern "C" int64_t sg_op_size(sg_op_t op) { return op ? op->n : -1; }
+
+extern "C" int sg_op_set_layers(sg_op_t op, int zl) {
+  if (!op) return sg_fail(SG_ERR_INVALID, "op_set_layers: NULL handle");
+  if (zl < 0) return sg_fail(SG_ERR_INVALID, "op_set_layers: zl must be >= 0");
+  op->g.zl = zl;
+  sg_pcg_release(op);   // cached graphs hold the old launch shape
+  return SG_OK;
+}
 
 extern "C" int sg_op_gll(sg_op_t op, double* nodes, double* weights) {
   if (!op) return sg_fail(SG_ERR_INVALID, "op_gll: NULL handle");

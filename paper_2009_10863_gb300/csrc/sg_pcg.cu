@@ -48,8 +48,9 @@ int sem_ctas(const SemGeom& g) {
     SG_CASE(1) SG_CASE(2) SG_CASE(3) SG_CASE(4) SG_CASE(5) SG_CASE(6) SG_CASE(7) SG_CASE(8)
 #undef SG_CASE
   }
-  int zl = sg_sem_layers(g, tex, tey, 0);
-  return ((g.ex + tex - 1) / tex) * ((g.ey + tey - 1) / tey) * ((g.ez + zl - 1) / zl);
+  // one layer per CTA: the most CTAs any layer count (sg_op_set_layers) gives,
+  // so a workspace sized before the count changes still holds the partials
+  return ((g.ex + tex - 1) / tex) * ((g.ey + tey - 1) / tey) * g.ez;
 }
 
 PcgLayout layout_for(sg_op_t op) {

@@ -72,6 +72,41 @@ def test_sem_apply_f32(sg, E, p, lam):
     assert np.all(got[~ref.interior] == 0.0)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_sem_apply_layers_per_cta(sg, dtype):
+    """The operator with 1, 2, 3 and all element layers per CTA (the z-carry
+    between layers, the ring of staged planes, and the single-layer FP64 PCG
+    step that stages the old p and q in idle ring slots) against the oracle."""
+    E, p, lam = (3, 2, 7), 7, 30.0
+    ref = SemOperator(*E, p, lam)
+    op = sg.Op(*E, p, lam, dtype)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    x = random_vectors(17, 1, ref.n)[0]
+    if dtype == "f32":
+        x = np.float32(x).astype(np.float64)
+    want = ref.apply(x)
+    tol = 1e-13 if dtype == "f64" else 1e-5
+    for zl in (1, 2, 3, 7, 0):
+        op.set_layers(zl)
+        assert rel(host(op.apply(dev(x, tdt))), want) <= tol, "zl = %d" % zl
+
+
+@pytest.mark.parametrize("zl", [1, 2, 4])
+def test_pcg_layers_per_cta(sg, zl):
+    """FP64 PCG with the operator on 1, 2 and 4 element layers per CTA: the
+    solution and the iteration count match the oracle's."""
+    ref, rng, xs = _problem((3, 2, 6), 5, 20.0, seed=8)
+    b = ref.apply(xs)
+    x0 = np.zeros(ref.n)
+    xo, ito, _, _ = opcg(ref.apply, ref.diagonal(), b, x0, 1e-10, interior=ref.interior)
+    op = sg.Op(3, 2, 6, 5, 20.0, "f64")
+    op.set_layers(zl)
+    x = dev(x0)
+    it, _ = op.pcg(dev(b), x, 1e-10)
+    assert abs(it - ito) <= 1
+    assert rel(host(x), xo) <= 1e-10
+
+
 @pytest.mark.parametrize("E,p,lam", MESHES[::3])
 def test_diagonal(sg, E, p, lam):
     ref = SemOperator(*E, p, lam)
