@@ -93,9 +93,28 @@ struct __align__(16) EOTab {
   using TL = SemTile<P>;
   T ce[TL::HE][TL::H];            // (C[a][l] + C[a][p-l]) / 2, a < H (+ middle row)
   T co[TL::H][TL::H];             // (C[a][l] - C[a][p-l]) / 2, a < H
-  T cm[TL::MID ? TL::HE : 1];     // C[a][mid] (odd line length only)
   T crow[P + 1];                  // row p of C: contribution to the next element's node 0
+  T cm[TL::MID ? TL::HE : 1];     // C[a][mid] (odd line length only)
 };
+
+// Copy n consecutive table entries into registers, 16 bytes per shared-memory
+// load when the run is 16-byte aligned and sized (rows of 4 floats or doubles).
+template <typename T, int N>
+__device__ __forceinline__ void load_run(const T* src, T (&dst)[N]) {
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+    constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+    for (int k = 0; k < N / PER; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(src)[k];
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int w = 0; w < PER; ++w) dst[k * PER + w] = e[w];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[k] = src[k];
+  }
+}
 
 // The 2p+1 tables a CTA uses, built once per operator on the host (sg_op.cu)
 // and copied into shared memory by every CTA:
@@ -122,17 +141,22 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1
   for (int l = 0; l < H; ++l) { s[l] = u[l] + u[P - l]; d[l] = u[l] - u[P - l]; }
 #pragma unroll
   for (int a = 0; a < H; ++a) {
-    T e = t.ce[a][0] * s[0];
+    T ce[H], co[H];
+    load_run<T, H>(t.ce[a], ce);
+    load_run<T, H>(t.co[a], co);
+    T e = ce[0] * s[0];
 #pragma unroll
-    for (int l = 1; l < H; ++l) e = fma(t.ce[a][l], s[l], e);
+    for (int l = 1; l < H; ++l) e = fma(ce[l], s[l], e);
     if constexpr (TL::MID) e = fma(t.cm[a], u[P / 2], e);
     T op = e;
 #pragma unroll
-    for (int l = 0; l < H; ++l) op = fma(t.co[a][l], d[l], op);
+    for (int l = 0; l < H; ++l) op = fma(co[l], d[l], op);
     o[P - a] = fma((T)2, e, -op);
     if (ROW && a == 0) {
+      T cr[P + 1];
+      load_run<T, P + 1>(t.crow, cr);
 #pragma unroll
-      for (int l = 0; l <= P; ++l) op = fma(t.crow[l], ul[l], op);
+      for (int l = 0; l <= P; ++l) op = fma(cr[l], ul[l], op);
     }
     o[a] = op;
   }
