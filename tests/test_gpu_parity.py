@@ -413,6 +413,39 @@ def test_proj_full_size(sg):
     assert rel(host(x0), o.form(b, np.zeros(ref.n))) <= 1e-12
 
 
+def test_headline_sequence_full_size(sg):
+    """The 16^3 p = 7 Helmholtz sequence with EXTRAP(2,8) and 1e-10, run as
+    the bench runs it (guess formed in the next ring slot, PCG as one graph
+    launch): every guess equals the oracle's extrapolation of the GPU's earlier
+    solutions, and at two sampled steps the oracle's PCG from the same guess
+    takes the same number of iterations (+-1) to the same solution."""
+    c = CONFIGS["c2"]
+    s, m, tol = c["s"], 2, c["tol"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+    cx, cy, cz = ref.coords_1d()
+    modes = Modes(c["seed"], c["modes"], c["kmax"])
+    g = sg.Guess(op.n, s, "extrap", m=m)
+    diag = ref.diagonal()
+    sols = []
+    for k in range(1, 11):
+        b = ref.apply(modes.field(cx, cy, cz, c["dt"] * k) * ref.interior)
+        x = g.next_slot()
+        g.form(dev(b), x)
+        x0 = host(x)
+        if sols:
+            beta = oex.startup_coeffs(len(sols), s, m)
+            assert rel(x0, oex.extrap_guess(sols[-s:], beta)) <= 1e-12, "guess at step %d" % k
+        it, _ = op.pcg(dev(b), x, tol)
+        xk = host(x)
+        if k in (4, 10):
+            xo, ito, _, _ = opcg(ref.apply, diag, b, x0, tol, interior=ref.interior)
+            assert abs(it - ito) <= 1, "iterations at step %d" % k
+            assert rel(xk, xo) <= (1e-10 if it == ito else 10 * tol)
+        g.update(x)
+        sols.append(xk)
+
+
 # ---------------------------------------------------------------- whole sequence
 def _gpu_sequence(sg, c, method, s, m, rhs, dtype="f64"):
     op = sg.Op(*c["E"], c["p"], c["lam"], dtype)
