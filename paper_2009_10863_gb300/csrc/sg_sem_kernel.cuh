@@ -307,21 +307,25 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     cp_async_commit();
   }
 
-  // FP64 PCG step over a single element layer: the p ring slots that no
-  // later layer needs take this layer's old q and p of the owned nodes (slot
-  // of plane c: q at [tid], p at [NT + tid]), copied asynchronously while the
-  // line products run (the FP32 kernel prefetches them into registers).
+  // FP64 over a single element layer: the p ring slots that no later layer
+  // needs take this layer's epilogue operands of the owned nodes -- PCG step:
+  // old q and p; residual: b and 1/diag -- (slot of plane c: the first at
+  // [tid], the second at [NT + tid]), copied asynchronously while the line
+  // products run (the FP32 kernel prefetches them into registers).
   constexpr bool PREF = sizeof(T) == 4;          // FP64: registers are too tight
-  constexpr bool SPF_FITS = 2 * NT <= PLANE;     // a slot holds one plane's q and p
-  const bool spf = SPF_FITS && !PREF && MODE == 1 && e1 == e0 + 1 && !*first_s;
+  constexpr bool SPF_FITS = 2 * NT <= PLANE;     // a slot holds one plane's two operands
+  const bool spf = SPF_FITS && !PREF && e1 == e0 + 1 && ((MODE == 1 && !*first_s) || MODE == 2);
   auto pq_slot = [&](int c) { return (e0 * P + P + 1 + c) % NPL; };
   if (spf) {
+    const T* src0 = MODE == 1 ? a.out : a.aux;
+    const T* src1 = MODE == 1 ? a.out2 : a.invd;
+    const bool two = MODE == 1 || !a.final_pass;   // the true-residual pass reads b only
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const size_t idx = colbase + nxy * (size_t)(e0 * P + c);
       T* sl = S + (size_t)pq_slot(c) * PLANE;
-      cp_async_elem(sl + tid, a.out + (col_in ? idx : 0), col_in);
-      cp_async_elem(sl + NT + tid, a.out2 + (col_in ? idx : 0), col_in);
+      cp_async_elem(sl + tid, src0 + (col_in ? idx : 0), col_in);
+      if (two) cp_async_elem(sl + NT + tid, src1 + (col_in ? idx : 0), col_in);
     }
     cp_async_commit();
   }
@@ -423,7 +427,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
     }
 
     // ---- combine, weights, epilogue
-    if (spf) cp_async_wait<0>();                 // this thread's own q and p copies
+    if (spf) cp_async_wait<0>();                 // this thread's own operand copies
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
@@ -446,11 +450,12 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
           a.out2[idx] = pv;
           red[0] += pv * qv;
         } else {
-          const T bv = inside ? (PREF ? ea[c] : a.aux[idx]) : (T)0;
+          const T* sl = S + (size_t)pq_slot(c) * PLANE;
+          const T bv = inside ? (PREF ? ea[c] : (spf ? sl[tid] : a.aux[idx])) : (T)0;
           const T rv = inside ? bv - yv : (T)0;
           a.out[idx] = rv;
           if (!a.final_pass) {
-            const T zv = rv * (PREF ? eb[c] : a.invd[idx]);
+            const T zv = rv * (PREF ? eb[c] : (spf ? sl[NT + tid] : a.invd[idx]));
             a.out2[idx] = zv;
             red[1] += rv * zv;
           }
