@@ -121,8 +121,38 @@ __global__ void k_inv_diag_cached(const SemGeom g, FastDiv dnx, FastDiv dnxy, in
   }
 }
 
-__global__ void k_set_diag_tag(PcgState* st, unsigned long long tag) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) st->diag_tag = tag;
+// The solve's small set-up in one launch: Dirichlet entries of x to 0
+// (as k_mask_faces) and, by block 0, the tag of the diagonal just ensured and
+// the state reset (as k_pcg_setup).  Runs after k_inv_diag_cached in stream order.
+template <typename T>
+__global__ void k_pcg_setup_all(T* x, int nx, int ny, int nz, PcgState* st, unsigned long long tag, double tol,
+                                int maxit, int criterion) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->diag_tag = tag;
+    st->rz = st->pq = st->rr = st->bb = st->rr0 = st->thr2 = 0.0;
+    st->alpha = st->beta = st->rr_true = 0.0;
+    st->iter = 0; st->done = 0; st->status = PCG_RUNNING; st->first = 1;
+    st->maxit = maxit; st->criterion = criterion; st->tol = tol;
+    st->xvec = x;
+    for (int i = 0; i < 4; ++i) st->counter[i] = 0u;
+  }
+  const size_t nxy = (size_t)nx * ny;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = t0; i < nx * ny; i += stride) {          // z faces
+    x[i] = (T)0;
+    x[(size_t)(nz - 1) * nxy + i] = (T)0;
+  }
+  for (int i = t0; i < nx * nz; i += stride) {          // y faces
+    int xi = i % nx, zi = i / nx;
+    x[(size_t)zi * nxy + xi] = (T)0;
+    x[(size_t)zi * nxy + (size_t)(ny - 1) * nx + xi] = (T)0;
+  }
+  for (int i = t0; i < ny * nz; i += stride) {          // x faces
+    int yi = i % ny, zi = i / ny;
+    x[(size_t)zi * nxy + (size_t)yi * nx] = (T)0;
+    x[(size_t)zi * nxy + (size_t)yi * nx + nx - 1] = (T)0;
+  }
 }
 
 __global__ void k_pcg_setup(PcgState* st, double tol, int maxit, int criterion, void* x) {
@@ -367,19 +397,15 @@ static int pcg_start(sg_op_t op, const T* b, T* x, double tol, int maxit, int cr
   T* invd = reinterpret_cast<T*>(ws + L.invd);
   const int n = (int)op->n;
   const SemGeom& g = op->g;
-  {
-    const unsigned long long tag = diag_tag(op);
-    int blocks = (n + 255) / 256;
-    if (blocks > 16 * sg_num_sms()) blocks = 16 * sg_num_sms();
-    k_inv_diag_cached<T><<<blocks, 256, 0, s>>>(g, op->div_nx, op->div_nxy, n, invd, st, tag);
-    SG_LAUNCH_CHECK("k_inv_diag_cached");
-    k_set_diag_tag<<<1, 32, 0, s>>>(st, tag);
-    SG_LAUNCH_CHECK("k_set_diag_tag");
-  }
-  k_mask_faces<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz);
-  SG_LAUNCH_CHECK("k_mask_faces");
-  k_pcg_setup<<<1, 32, 0, s>>>(st, tol, maxit, criterion, x);
-  SG_LAUNCH_CHECK("k_pcg_setup");
+  const unsigned long long tag = diag_tag(op);
+  // one wave (2 CTAs per SM): when the workspace holds the diagonal already,
+  // every CTA only reads the tag and returns
+  int blocks = (n + 255) / 256;
+  if (blocks > 2 * sg_num_sms()) blocks = 2 * sg_num_sms();
+  k_inv_diag_cached<T><<<blocks, 256, 0, s>>>(g, op->div_nx, op->div_nxy, n, invd, st, tag);
+  SG_LAUNCH_CHECK("k_inv_diag_cached");
+  k_pcg_setup_all<T><<<64, 256, 0, s>>>(x, g.nx, g.ny, g.nz, st, tag, tol, maxit, criterion);
+  SG_LAUNCH_CHECK("k_pcg_setup_all");
   SemArgs<T> a{};
   a.x = x; a.aux = b; a.invd = invd; a.out = reinterpret_cast<T*>(ws + L.r); a.out2 = reinterpret_cast<T*>(ws + L.z);
   a.partials = reinterpret_cast<double*>(ws + L.partials); a.st = st; a.final_pass = 0;
