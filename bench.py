@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
-PCG_APPLY_TRAFFIC = 34390528 + 768  # read + write of the not-first MODE 1 launch
+PCG_APPLY_TRAFFIC = 34040320 + 0  # read + write of the not-first MODE 1 launch
 
 
 def aggregate_max(value, dist, device):
