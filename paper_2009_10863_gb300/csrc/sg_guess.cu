@@ -191,18 +191,20 @@ __device__ __forceinline__ void dots_body(const T* base, size_t stride, const T*
 }
 
 // form, pass 1: alpha_j = scale_j * (slot_j . b), j < d
+// The reductions carry DMAX values (+ a norm) rather than SG_SMAX: the block
+// sum costs about as many additions per thread as the padded value count.
 template <typename T, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_dots(const ProjArgs<T> a) {
-  __shared__ double sred[32 * SG_SMAX];
+  __shared__ double sred[32 * DMAX];
   const int d = a.st->d;
-  double v[SG_SMAX], tot[SG_SMAX];
+  double v[DMAX], tot[DMAX];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
+  for (int j = 0; j < DMAX; ++j) v[j] = 0.0;
   const T* partner = a.energy ? a.X : a.B;   // energy: alpha = X~^T b = (X~, A^{-1} b)_A
 #define SG_CALL(D) dots_body<T, D>(partner, a.stride, a.v, a.n, v)
   SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
-  if (grid_reduce_last<SG_SMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  if (grid_reduce_last<DMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->alpha[j] = a.st->scale[j] * tot[j];
   }
@@ -339,9 +341,9 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
   }
 }
 
-template <typename T, int D, bool EN>
+template <typename T, int D, bool EN, int N>
 __device__ __forceinline__ void givens_body(const ProjArgs<T>& a, const GivensCoef<T>& gr, bool fast,
-                                            double (&v)[NV]) {
+                                            double (&v)[N]) {
   T acc[SG_NZ(D)];
 #pragma unroll
   for (int j = 0; j < D; ++j) acc[j] = 0;
@@ -382,7 +384,8 @@ template <typename T, bool EN, int DMAX>
 // flight, and the extra CTA beats the few spills it costs (measured: QR(8)
 // update sweeps 284 -> 267 us at 1.44M nodes)
 __global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
-  __shared__ double sred[32 * NV];
+  constexpr int RV = DMAX + 1;           // dots, then ||t||^2 at [DMAX]
+  __shared__ double sred[32 * RV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
   __shared__ GivensCoef<T> gr;
   __shared__ double s_sc[SG_SMAX];      // column scales before the downdate
@@ -473,9 +476,9 @@ __global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
     __syncthreads();
     d -= 1;   // columns the new vector is projected on
   }
-  double v[NV], tot[NV];
+  double v[RV], tot[RV];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int j = 0; j < RV; ++j) v[j] = 0.0;
   if (rot) {
 #define SG_CALL(D) givens_body<T, D, EN>(a, gr, fast, v)
     SG_COLS_DISPATCH_UPTO(DMAX - 1, d, SG_CALL)   // d - 1 < M <= DMAX rotations
@@ -485,8 +488,8 @@ __global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
     SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
   }
-  v[SG_SMAX] = (double)vdot<T>(EN ? a.v : a.t, a.t, a.n);
-  if (grid_reduce_last<NV>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  v[DMAX] = (double)vdot<T>(EN ? a.v : a.t, a.t, a.n);
+  if (grid_reduce_last<RV>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (tid == 0) {
       ProjState* st = a.st;
       if (rot) {
@@ -500,14 +503,14 @@ __global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
       }
       st->d = d;
       st->rotated = rot;
-      st->nrm0sq = tot[SG_SMAX];
+      st->nrm0sq = tot[DMAX];
     }
   }
 }
 
 // t -= sum_j c_j B_j (D columns), then v[j] = B_j . t (energy: X_j . t)
-template <typename T, int D, bool EN>
-__device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[SG_SMAX]) {
+template <typename T, int D, bool EN, int N>
+__device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_SMAX], double (&v)[N]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   T acc[SG_NZ(D)];
@@ -549,18 +552,18 @@ __device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_
 // update sweep 2: t -= B~ c1; c2 = B~^T t (energy: X~^T t)
 template <typename T, bool EN, int DMAX>
 __global__ void __launch_bounds__(256) k_proj_upd2(const ProjArgs<T> a) {
-  __shared__ double sred[32 * SG_SMAX];
+  __shared__ double sred[32 * DMAX];
   const int d = a.st->d;
   T c[SG_SMAX];
 #pragma unroll
   for (int j = 0; j < SG_SMAX; ++j) c[j] = (j < d) ? (T)(a.st->c1[j] * a.st->scale[j]) : (T)0;
-  double v[SG_SMAX], tot[SG_SMAX];
+  double v[DMAX], tot[DMAX];
 #pragma unroll
-  for (int j = 0; j < SG_SMAX; ++j) v[j] = 0.0;
+  for (int j = 0; j < DMAX; ++j) v[j] = 0.0;
 #define SG_CALL(D) upd2_body<T, D, EN>(a, c, v)
   SG_COLS_DISPATCH_UPTO(DMAX, d, SG_CALL)
 #undef SG_CALL
-  if (grid_reduce_last<SG_SMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
+  if (grid_reduce_last<DMAX>(v, a.partials, &a.st->counter[0], sred, tot)) {
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) a.st->c2[j] = a.st->scale[j] * tot[j];
   }
