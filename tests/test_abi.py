@@ -101,3 +101,23 @@ def test_argument_errors_without_a_device(sg):
     assert L.sg_guess_workspace_bytes(n, 8, sg.PROJ_ENERGY, sg.F64) == L.sg_guess_workspace_bytes(n, 8, sg.PROJ_QR,
                                                                                                    sg.F64)
     assert L.sg_guess_workspace_bytes(n, 8, 7, sg.F64) == 0
+
+
+def test_layer_knob_and_deviceless_operator(sg):
+    """sg_op_set_layers validates its arguments; on a host without a CUDA
+    device an operator still answers the host queries but refuses launches."""
+    L = sg.lib()
+    assert L.sg_op_set_layers(None, 1) == sg.ERR_INVALID
+    h = ctypes.c_void_p()
+    assert L.sg_op_create(ctypes.byref(h), 2, 2, 3, 4, 1.0, sg.F64) == 0
+    assert L.sg_op_set_layers(h, -1) == sg.ERR_INVALID
+    assert b"zl" in L.sg_last_error()
+    for zl in (0, 1, 2, 7):
+        assert L.sg_op_set_layers(h, zl) == 0
+    assert L.sg_op_size(h) == (2 * 4 + 1) * (2 * 4 + 1) * (3 * 4 + 1)
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        VP = ctypes.c_void_p
+        assert L.sg_sem_apply(h, VP(256), VP(512), None) == sg.ERR_STATE
+        assert b"without a CUDA device" in L.sg_last_error()
+    assert L.sg_op_destroy(h) == 0
