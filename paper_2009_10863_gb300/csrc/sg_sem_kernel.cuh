@@ -12,25 +12,31 @@
 // paper's local operator).  C is centrosymmetric (C[p-a][p-l] = C[a][l]), so
 // each line uses the even-odd split: s_l = u_l + u_{p-l}, d_l = u_l - u_{p-l},
 // o_a = E_a + O_a, o_{p-a} = E_a - O_a with two half-size products -- about
-// 3/4 of the multiply-adds of the plain product, and no divergent branches.
+// 3/4 of the multiply-adds of the plain product, and no divergent branches
+// (the odd sum is accumulated onto E_a, and o_{p-a} = 2 E_a - o_a).
 // The contribution of the element before a shared node (row p of C on its
 // line) is added by the line that owns the node, so every output node is
-// written exactly once, without atomics or a scatter pass.
+// written exactly once, without atomics or a scatter pass.  The weight W_k of
+// an output's z index sits in the coefficient tables (sem_tables), so the
+// epilogue multiplies by W_i W_j only.
 //
 // Tiling.  A CTA owns TEX x TEY elements in x,y (TX x TY nodes, one thread per
 // (x,y) column) and marches through ZL element layers in z.  For each layer the
 // p+1 planes z = e p .. e p + p sit in shared memory, padded by p nodes below
 // and 1 above in x and y (the top plane is reused as the next layer's bottom).
 // Planes are staged with cp.async (zero-filled outside the interior) into a
-// ring of 2p+1 slots, so the next layer's planes load while this one computes.
+// ring of 2p+1 slots, so the next layer's planes load while this one computes;
+// a CTA of one layer (FP64) uses the p slots no later layer needs for its
+// epilogue operands (old q, p; or b, 1/diag), also by cp.async.
 //   z: each thread contracts its own column in registers; the top output of a
 //      layer is carried to the next layer's bottom node;
 //   x: item (plane c, row y, element) -> p outputs written to a work buffer;
 //   y: item (plane c, column x, element) -> p outputs; FP64 adds them to the
 //      x results in the same buffer (three barriers per layer), FP32 writes a
 //      second buffer (two barriers);
-// the thread then adds its column's x and y results, the mass term and the
-// weights, and stores.  The upper Dirichlet faces (index n-1) are written 0.
+// the thread then adds its column's x and y results (the mass term is in the
+// z table), multiplies by W_i W_j, and stores.  The upper Dirichlet faces
+// (index n-1) are written 0.
 //
 // MODE 0: out = A x.
 // MODE 1: PCG step (Sec. 5.3) on the staged z: w = A z, then for owned nodes
