@@ -17,7 +17,7 @@
  *  - Workspaces are DEVICE buffers owned by the caller, sized by the matching
  *    *_workspace_bytes() query, 256-byte aligned, and must outlive the handle
  *    (guess) or the call (PCG).  The library allocates only the small
- *    per-operator coefficient tables (sg_op_create, < 4 KB), the instantiated
+ *    per-operator coefficient tables (sg_op_create, < 8 KB), the instantiated
  *    PCG iteration graphs it caches on an operator (at most 8 per operator,
  *    released by sg_op_destroy) and one pinned host word per host thread for
  *    convergence polls.
