@@ -272,7 +272,8 @@ def test_zero_guess(sg):
 
 
 # ---------------------------------------------------------------- projection
-def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dtype="f64", xscale=1.0):
+def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dtype="f64", xscale=1.0,
+                   bounded=False):
     ref = SemOperator(*E, p, lam)
     op = sg.Op(*E, p, lam, dtype)
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -294,7 +295,8 @@ def _proj_sequence(sg, klass, method, M, E=(3, 3, 2), p=3, lam=2.0, steps=10, dt
         if k == 6:   # a combination of earlier solutions (rejected when in the window)
             x = 0.5 * prev[-1] + 0.25 * prev[-2]
         else:
-            x = (np.cos(0.3 * k) * base[0] + np.sin(0.2 * k) * base[1] + 0.1 * k * base[2]
+            c2 = np.cos(0.07 * k + 1.0) if bounded else 0.1 * k   # bounded: long runs stay well conditioned
+            x = (np.cos(0.3 * k) * base[0] + np.sin(0.2 * k) * base[1] + c2 * base[2]
                  + 1e-3 * rng.standard_normal(ref.n) * ref.interior) * xscale
         if dtype == "f32":
             x = np.float32(x).astype(np.float64)
@@ -317,6 +319,15 @@ def test_proj_qr_long_sequence(sg):
     """40 steps of QR(4): 36 Givens downdates in the factored form, whose
     column scales are carried from step to step."""
     _proj_sequence(sg, ProjectionQR, "qr", 4, steps=40)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_proj_qr_very_long_sequence(sg, dtype):
+    """300 steps of QR(3): the column scales of the factored downdate drift by
+    the factors taken out at every step, and the plain-form launch that resets
+    them (FP32 storage: once a scale leaves 2^+-40) must keep the guesses on
+    the oracle's."""
+    _proj_sequence(sg, ProjectionQR, "qr", 3, steps=300, dtype=dtype, bounded=True)
 
 
 @pytest.mark.parametrize("method,klass", [("qr", ProjectionQR), ("energy", ProjectionEnergy)])
