@@ -323,10 +323,8 @@ def test_proj_qr_long_sequence(sg):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_proj_qr_very_long_sequence(sg, dtype):
-    """300 steps of QR(3): the column scales of the factored downdate drift by
-    the factors taken out at every step, and the plain-form launch that resets
-    them (FP32 storage: once a scale leaves 2^+-40) must keep the guesses on
-    the oracle's."""
+    """300 steps of QR(3): the column scales of the factored downdate are
+    carried through 297 downdates and the guesses stay on the oracle's."""
     _proj_sequence(sg, ProjectionQR, "qr", 3, steps=300, dtype=dtype, bounded=True)
 
 
@@ -335,6 +333,12 @@ def test_proj_sequence_tiny_values(sg, method, klass):
     """Solutions of size ~1e-100 give column scales ~1e100, outside the range
     the factored downdate keeps; the downdate then runs in the plain form."""
     _proj_sequence(sg, klass, method, 3, xscale=1e-100)
+
+
+def test_proj_sequence_tiny_values_f32(sg):
+    """FP32 storage keeps scales within 2^+-40: solutions of size ~1e-15
+    (scales ~1e15) send every downdate through the plain form."""
+    _proj_sequence(sg, ProjectionQR, "qr", 3, xscale=1e-15, dtype="f32")
 
 
 def test_proj_qr_sequence_f32(sg):
