@@ -3,6 +3,7 @@ mesh of the bench's shapes, for profiling (ncu) and quick timing.
 
     python -m paper_2009_10863_gb300.profile_run --elements 16 --dtype f64
     python -m paper_2009_10863_gb300.profile_run --steps 6
+    python -m paper_2009_10863_gb300.profile_run --batched
 
 The first form applies the operator `--reps` times (timed with CUDA events),
 runs a few PCG iterations (host-launched, as with kernel timing on), forms an
@@ -10,7 +11,8 @@ EXTRAP(2,8) guess and performs QR(8) history updates.  The second runs time
 steps of bench.py's main sequence (FP64 16^3 p = 7 Helmholtz, EXTRAP(2,8),
 1e-10) with every library launch timed by CUDA events, so that the PCG
 iterations are host launches that a profiler lists one by one (bench.py's
-timed steps run them inside CUDA-graph WHILE loops).
+timed steps run them inside CUDA-graph WHILE loops).  The third solves the
+four batched systems once (the persistent kernel, one launch per iteration).
 """
 import argparse
 
@@ -30,11 +32,14 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=6)
     ap.add_argument("--s", type=int, default=8)
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--batched", action="store_true")
     args = ap.parse_args()
     from paper_2009_10863_gb300 import build
     build.build()
     if args.steps > 0:
         return sequence_steps(args.steps)
+    if args.batched:
+        return batched_solve()
     E = args.elements
     op = sg.Op(E, E, E, args.p, args.lam, args.dtype)
     gen = torch.Generator(device="cuda").manual_seed(0)
@@ -69,6 +74,27 @@ def main():
     print("nodes %d dtype %s apply %.1f us, pcg iterations %d (step %.1f us, update %.1f us), qr d=%d" %
           (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, 1e3 * t_apply / max(n_apply, 1),
            1e3 * t_upd / max(n_upd, 1), q.info()[0]))
+
+
+def batched_solve():
+    """One solve of the four batched systems (24^3 Poisson, 20^3, 16^3, 12^3
+    Helmholtz, p = 7; FP32 PCG in FP64 refinement, one persistent launch per
+    CG iteration) from zero, right-hand sides A x for random x; no tuning."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from synthetic import BATCHED
+    meshes = [(c["E"][0], c["E"][1], c["E"][2], c["lam"]) for c in BATCHED]
+    solver = sg.BatchSolver(meshes)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    bs, xs = [], []
+    for c in BATCHED:
+        op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+        bs.append(op.apply(torch.randn(op.n, dtype=torch.float64, device="cuda", generator=gen)))
+        xs.append(op.zeros())
+    outer, inner, rel = solver.solve(bs, xs, 1e-10)
+    torch.cuda.synchronize()
+    print("batched: outer", outer, "inner", inner, "relres %.2e" % max(rel))
 
 
 def sequence_steps(steps):
