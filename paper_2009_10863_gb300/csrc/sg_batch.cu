@@ -82,6 +82,10 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err, unsign
 template <int NV>
 __device__ __forceinline__ void block_sum_2d(double (&v)[NV], double* smem) { block_sum<NV>(v, smem); }
 
+// COND: the launch is the body of a conditional WHILE node and sets its
+// condition; the other instantiation (replay graphs) contains no conditional
+// call, which keeps its graph nodes visible to kernel profilers.
+template <bool COND>
 __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_constant__ BatchArgs A) {
   constexpr int NS = SG_BATCH_MAX;
   __shared__ float s_beta[NS];
@@ -109,7 +113,9 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
   }
   __syncthreads();
   if (s_all_done) {         // uniform over the grid: no barrier is entered
-    if (A.use_cond && blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(A.cond, 0u);
+    if constexpr (COND) {
+      if (A.use_cond && blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(A.cond, 0u);
+    }
     return;
   }
 
@@ -232,11 +238,13 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
           if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
         }
       }
-      if (A.use_cond) {       // continue while a system runs and no barrier wait expired
-        int more = 0;
-        for (int s = 0; s < A.nseq; ++s) more |= !A.seq[s].st->done;
-        if (*(volatile int*)A.err) more = 0;
-        cudaGraphSetConditional(A.cond, more ? 1u : 0u);
+      if constexpr (COND) {
+        if (A.use_cond) {     // continue while a system runs and no barrier wait expired
+          int more = 0;
+          for (int s = 0; s < A.nseq; ++s) more |= !A.seq[s].st->done;
+          if (*(volatile int*)A.err) more = 0;
+          cudaGraphSetConditional(A.cond, more ? 1u : 0u);
+        }
       }
     }
   }
@@ -357,6 +365,7 @@ struct sg_batch_s {
   cudaGraphExec_t graph;
   int graph_ready;
   int graph_while;          // 1: the graph is one WHILE node (one launch per solve)
+  int graph_prof;           // the graph was built while kernel timing was on (replay form)
   cudaStream_t graph_stream;
 };
 
@@ -464,7 +473,8 @@ int launch_iter(sg_batch_t b, cudaStream_t s, cudaGraphConditionalHandle cond = 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_batch_iter, params);
+  const void* fn = use_cond ? (const void*)k_batch_iter<true> : (const void*)k_batch_iter<false>;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, fn, params);
   sg_count_launch();
   if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("batch iteration launch: ") + cudaGetErrorString(e));
   return SG_OK;
@@ -473,12 +483,18 @@ int launch_iter(sg_batch_t b, cudaStream_t s, cudaGraphConditionalHandle cond = 
 int max_coresident(int* per_sm) {
   static int cached = -1;
   if (cached < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
+    // both instantiations: the grid must be co-resident for either
+    cudaError_t e = cudaFuncSetAttribute(k_batch_iter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_batch_iter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
     if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("batch smem attribute: ") + cudaGetErrorString(e));
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_iter, BTile::NTHREADS, batch_smem());
-    if (e != cudaSuccess || nb < 1) return sg_fail(SG_ERR_CUDA, "batch occupancy query failed");
-    cached = nb;
+    int nb = 0, nb2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_iter<true>, BTile::NTHREADS, batch_smem());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_batch_iter<false>, BTile::NTHREADS, batch_smem());
+    if (e != cudaSuccess || nb < 1 || nb2 < 1) return sg_fail(SG_ERR_CUDA, "batch occupancy query failed");
+    cached = nb < nb2 ? nb : nb2;
   }
   *per_sm = cached;
   return SG_OK;
@@ -518,6 +534,7 @@ extern "C" int sg_batch_create(sg_batch_t* out, int nseq, const sg_op_t* ops64, 
   b->graph_iters = 8;
   b->graph_ready = 0;
   b->graph_while = 0;
+  b->graph_prof = 0;
   int per_sm = 0;
   int rc = max_coresident(&per_sm);
   if (rc) { delete b; return rc; }
@@ -560,7 +577,11 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
   // conditional WHILE node around one persistent launch (CTA 0 of every
   // iteration sets the condition; one graph launch runs the whole solve),
   // else graph_iters launches replayed until every system is done.
-  if (!b->graph_ready || b->graph_stream != s) {
+  // With kernel timing on (sg_profile_enable) the replay form is built: its
+  // kernel nodes are visible one by one to profilers, which do not look
+  // inside graphs with conditional nodes.
+  const int prof = sg_profiling_on() ? 1 : 0;
+  if (!b->graph_ready || b->graph_stream != s || b->graph_prof != prof) {
     if (b->graph_ready) { cudaGraphExecDestroy(b->graph); b->graph_ready = 0; }
     cudaStream_t cs;
     SG_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -570,7 +591,7 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
     cudaGraphConditionalHandle cond = 0;
     cudaGraphNodeParams cp = {};
     cudaGraphNode_t node;
-    cudaError_t e = cudaGraphCreate(&graph, 0);
+    cudaError_t e = prof ? cudaErrorNotSupported : cudaGraphCreate(&graph, 0);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
       cp.type = cudaGraphNodeTypeConditional;
@@ -612,6 +633,7 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
     if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     b->graph_ready = 1;
     b->graph_stream = s;
+    b->graph_prof = prof;
   }
   PollS poll[SG_BATCH_MAX];
   int done_all = 0, replays = 0;

@@ -92,8 +92,10 @@ def batched_solve():
         op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
         bs.append(op.apply(torch.randn(op.n, dtype=torch.float64, device="cuda", generator=gen)))
         xs.append(op.zeros())
+    sg.profile_enable(True)      # replay form: the persistent launches are plain graph kernel nodes
     outer, inner, rel = solver.solve(bs, xs, 1e-10)
     torch.cuda.synchronize()
+    sg.profile_enable(False)
     print("batched: outer", outer, "inner", inner, "relres %.2e" % max(rel))
 
 
