@@ -346,6 +346,19 @@ void* sg_guess_next_slot(sg_guess_t g);
  * PROJ_CLASSIC: Algorithm 1 after the solve.  b is not read. */
 int sg_guess_update(sg_guess_t g, const void* x, const void* b, void* stream);
 
+/* Checkpoint of a guess handle (no counterpart in the paper; a time stepper
+ * that restarts needs its history back).  sg_guess_image_bytes: size of the
+ * HOST image (a header plus the handle's workspace contents: history columns,
+ * projection state and R), 0 for a NULL handle.  sg_guess_export writes the
+ * image to ``image`` (HOST, caller-owned); sg_guess_import restores it into a
+ * handle created with the same n, s, method, degree and dtype (its own
+ * workspace), after which form/update continue exactly as they would have in
+ * the exported handle.  Both synchronise with ``stream``.  SG_ERR_INVALID for
+ * NULL arguments or an image of another kind of handle. */
+size_t sg_guess_image_bytes(sg_guess_t g);
+int sg_guess_export(sg_guess_t g, void* image, void* stream);
+int sg_guess_import(sg_guess_t g, const void* image, void* stream);
+
 /* Debug/inspection (synchronises ``stream``): current history dimension d
  * (PROJ) or stored-solution count (EXTRAP), and, if R is not NULL, the
  * s*s row-major FP64 factor R (PROJ) or the current s coefficients beta

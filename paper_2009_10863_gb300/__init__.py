@@ -53,6 +53,9 @@ SIGNATURES = [
     ("sg_guess_next_slot", _VP, [_VP]),
     ("sg_guess_update", _I, [_VP, _VP, _VP, _VP]),
     ("sg_guess_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    ("sg_guess_image_bytes", _SZ, [_VP]),
+    ("sg_guess_export", _I, [_VP, _VP, _VP]),
+    ("sg_guess_import", _I, [_VP, _VP, _VP]),
     ("sg_profile_enable", _I, [_I]),
     ("sg_profile_read", _I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     ("sg_profile_reset", _I, []),
@@ -294,6 +297,17 @@ class Guess:
 
     def update(self, x, b=None):
         _check(lib().sg_guess_update(self.h, _ptr(x), _ptr(b) if b is not None else None, _stream()))
+
+    def export(self):
+        """Host image of the history (numpy uint8 array) -- synchronises."""
+        img = np.empty(int(lib().sg_guess_image_bytes(self.h)), dtype=np.uint8)
+        _check(lib().sg_guess_export(self.h, img.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return img
+
+    def restore(self, image):
+        """Load a history exported by a handle with the same parameters."""
+        img = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(lib().sg_guess_import(self.h, img.ctypes.data_as(ctypes.c_void_p), _stream()))
 
     def info(self):
         """(d, R or beta as an s x s / s array) -- synchronises."""

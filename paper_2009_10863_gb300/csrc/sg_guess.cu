@@ -907,6 +907,60 @@ extern "C" int sg_guess_update(sg_guess_t g, const void* x, const void* b, void*
   return g->dtype == SG_F64 ? proj_update<double>(g, x, s) : proj_update<float>(g, x, s);
 }
 
+// ---------------------------------------------------------------- checkpoint
+// Host image of a guess handle: a header (handle parameters and the ring
+// position the host keeps) followed by the workspace bytes (history columns,
+// projection state and R on the device).
+namespace {
+struct GuessImageHeader {
+  uint64_t magic;
+  int64_t n;
+  int32_t method, s, m, dtype, count, next;
+  uint64_t ws_bytes;
+};
+constexpr uint64_t kGuessImageMagic = 0x5347475545535331ull;
+}  // namespace
+
+extern "C" size_t sg_guess_image_bytes(sg_guess_t g) {
+  if (!g) return 0;
+  return sizeof(GuessImageHeader) + guess_layout(g->n, g->s, g->method, g->dtype).total;
+}
+
+extern "C" int sg_guess_export(sg_guess_t g, void* image, void* stream) {
+  if (!g || !image) return sg_fail(SG_ERR_INVALID, "guess_export: NULL argument");
+  const size_t total = guess_layout(g->n, g->s, g->method, g->dtype).total;
+  GuessImageHeader h{};
+  h.magic = kGuessImageMagic;
+  h.n = g->n; h.method = g->method; h.s = g->s; h.m = g->m; h.dtype = g->dtype;
+  h.count = g->count; h.next = g->next; h.ws_bytes = total;
+  std::memcpy(image, &h, sizeof(h));
+  cudaStream_t s = as_stream(stream);
+  if (total > 0)
+    SG_CUDA_TRY(cudaMemcpyAsync(static_cast<unsigned char*>(image) + sizeof(h), g->ws, total,
+                                cudaMemcpyDeviceToHost, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  return SG_OK;
+}
+
+extern "C" int sg_guess_import(sg_guess_t g, const void* image, void* stream) {
+  if (!g || !image) return sg_fail(SG_ERR_INVALID, "guess_import: NULL argument");
+  GuessImageHeader h;
+  std::memcpy(&h, image, sizeof(h));
+  const size_t total = guess_layout(g->n, g->s, g->method, g->dtype).total;
+  if (h.magic != kGuessImageMagic) return sg_fail(SG_ERR_INVALID, "guess_import: not a guess image");
+  if (h.n != g->n || h.method != g->method || h.s != g->s || h.m != g->m || h.dtype != g->dtype ||
+      h.ws_bytes != total)
+    return sg_fail(SG_ERR_INVALID, "guess_import: image of a handle with other n, s, method, degree or dtype");
+  cudaStream_t s = as_stream(stream);
+  if (total > 0)
+    SG_CUDA_TRY(cudaMemcpyAsync(g->ws, static_cast<const unsigned char*>(image) + sizeof(h), total,
+                                cudaMemcpyHostToDevice, s));
+  SG_CUDA_TRY(cudaStreamSynchronize(s));
+  g->count = h.count;
+  g->next = h.next;
+  return SG_OK;
+}
+
 extern "C" int sg_guess_info(sg_guess_t g, int* d, double* R, void* stream) {
   if (!g) return sg_fail(SG_ERR_INVALID, "guess_info: NULL handle");
   cudaStream_t s = as_stream(stream);

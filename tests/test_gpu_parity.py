@@ -264,6 +264,37 @@ def test_extrap_inplace_guess_into_next_slot(sg):
     assert rel(host(slot), want) <= 1e-12
 
 
+@pytest.mark.parametrize("method", ["extrap", "qr", "energy"])
+def test_guess_checkpoint_restore(sg, method):
+    """A history exported after five updates and restored into a fresh handle
+    (its own workspace) forms the same guesses, bit for bit, as the original
+    over three further steps; an image of another kind of handle is refused."""
+    E, p, lam = (3, 2, 2), 4, 3.0
+    op = sg.Op(*E, p, lam, "f64")
+    rng = np.random.default_rng(41)
+    mask = host(op.apply(dev(np.ones(op.n)))) != 0.0
+    xs = [dev(rng.standard_normal(op.n) * mask) for _ in range(8)]
+    bs = [dev(rng.standard_normal(op.n) * mask) for _ in range(3)]
+    kw = dict(m=2) if method == "extrap" else dict(eps_rel=1e-10, op=op)
+    g = sg.Guess(op.n, 4, method, **kw)
+    for x in xs[:5]:
+        g.update(x.clone())
+    image = g.export()
+    h = sg.Guess(op.n, 4, method, **kw)
+    h.restore(image)
+    for k in range(3):
+        x0g, x0h = op.zeros(), op.zeros()
+        g.form(bs[k], x0g)
+        h.form(bs[k], x0h)
+        assert torch.equal(x0g, x0h), "guess %d" % k
+        g.update(xs[5 + k].clone())
+        h.update(xs[5 + k].clone())
+    assert g.info()[0] == h.info()[0]
+    other = sg.Guess(op.n, 3, method, **kw)
+    with pytest.raises(sg.SGError):
+        other.restore(image)
+
+
 def test_zero_guess(sg):
     g = sg.Guess(100, 4, "zero")
     x0 = torch.ones(100, dtype=torch.float64, device="cuda")
