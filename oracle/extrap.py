@@ -55,12 +55,14 @@ def lsq_coeffs(M, m):
     return Q @ y
 
 
-def sparse_coeffs(M, m):
-    """beta for SPEXTRAP(m, M) by Eq. CPQRCoeffs (column-pivoted QR of V^T)."""
-    if M < 1 or m < 0 or m > M - 1:
-        raise ValueError("need 0 <= m <= M-1")
-    if M == 1:
-        return np.array([1.0])
+def _cpqr(M, m):
+    """Column-pivoted Householder QR of V^T (Sec. 3.3, Eq. CPQRCoeffs).
+
+    Returns the pivot order (time-point indices, first pivot first) and the
+    m+1 non-zero coefficients R_hat^{-1} Q^T v in that order.  Pivot j is the
+    remaining column of largest 2-norm below row j, i.e. the time point whose
+    Legendre vector psi(t_i) is farthest from the span of the points already
+    chosen (Businger & Golub, Numer. Math. 7, 1965)."""
     t, tn = time_points(M)
     VT = vandermonde(t, m).T.copy()      # (m+1) x M
     v = vandermonde([tn], m)[0]
@@ -88,9 +90,28 @@ def sparse_coeffs(M, m):
             Qt[j:, :] -= 2.0 * np.outer(u, u @ Qt[j:, :])
     Rhat = np.triu(A[:, :k])
     bhat = np.linalg.solve(Rhat, Qt @ v)
+    return perm[:k], bhat
+
+
+def sparse_pivots(M, m):
+    """Time-point indices (0 = oldest) chosen by the pivoted QR, in pivot order."""
+    if M < 1 or m < 0 or m > M - 1:
+        raise ValueError("need 0 <= m <= M-1")
+    if M == 1:
+        return [0]
+    return _cpqr(M, m)[0]
+
+
+def sparse_coeffs(M, m):
+    """beta for SPEXTRAP(m, M) by Eq. CPQRCoeffs (column-pivoted QR of V^T)."""
+    if M < 1 or m < 0 or m > M - 1:
+        raise ValueError("need 0 <= m <= M-1")
+    if M == 1:
+        return np.array([1.0])
+    piv, bhat = _cpqr(M, m)
     beta = np.zeros(M)
-    for j in range(k):
-        beta[perm[j]] = bhat[j]
+    for j, i in enumerate(piv):
+        beta[i] = bhat[j]
     return beta
 
 

@@ -381,3 +381,60 @@ def test_lebesgue_curves_golden_and_bounds():
         assert lam_lsq <= lam_naive + 1e-9 and lam_sp <= lam_naive + 1e-9
         if m < M - 1:
             assert lam_lsq < lam_naive
+
+
+# ---------------------------------------------------------------- sparse extrapolation pivots
+def _greedy_farthest_points(M, m, tie_rel=1e-9):
+    """Brute force of the pivot rule of Eq. CPQRCoeffs, independent of any QR:
+    pivot k is the time point whose Legendre vector psi(t_i) = V^T e_i lies
+    farthest (2-norm) from the span of the points already chosen, the distance
+    taken from a dense least-squares fit; equal distances go to the most recent
+    point.  Returns the pivot order and, per pivot, the relative margin between
+    the winner's distance and the best distance that is not tied with it."""
+    t, _ = ex.time_points(M)
+    VT = ex.vandermonde(t, m).T
+    chosen, margins = [], []
+    for _ in range(m + 1):
+        dist = {}
+        for i in range(M):
+            if i in chosen:
+                continue
+            col = VT[:, i]
+            if chosen:
+                B = VT[:, chosen]
+                coef, *_ = np.linalg.lstsq(B, col, rcond=None)
+                col = col - B @ coef
+            dist[i] = float(np.linalg.norm(col))
+        best = max(dist.values())
+        tied = [i for i, d in dist.items() if d >= best * (1.0 - tie_rel)]
+        rest = [d for i, d in dist.items() if i not in tied]
+        margins.append((best - max(rest)) / best if rest else 1.0)
+        chosen.append(max(tied))
+    return chosen, margins
+
+
+@pytest.mark.parametrize("M,m", [(4, 1), (6, 1), (8, 2), (10, 2), (12, 3), (16, 3), (16, 4), (12, 5), (8, 7)])
+def test_sparse_pivots_are_greedy_farthest_points(M, m):
+    """The oracle's column-pivoted QR picks, pivot by pivot, the same time points
+    as the brute-force greedy rule (largest distance to the span of the chosen
+    columns, ties to the most recent point).  Every non-tied runner-up is far
+    from the winner, so the tie tolerance cannot decide the outcome."""
+    want, margins = _greedy_farthest_points(M, m)
+    assert min(margins) > 1e-6
+    assert ex.sparse_pivots(M, m) == want
+    assert sorted(np.flatnonzero(ex.sparse_coeffs(M, m)).tolist()) == sorted(want)
+
+
+@pytest.mark.parametrize("M,m", [(8, 2), (12, 3), (16, 4), (16, 3), (12, 5)])
+def test_sparse_points_cluster_at_the_ends(M, m):
+    """Sec. 3.3: the chosen points show the end-point clustering of Chebyshev
+    points -- both ends of the window are taken first (their Legendre vectors
+    are the longest, |P_j(+-1)| = 1 >= |P_j(t)|), the most recent before the
+    oldest, and no gap between chosen points next to an end is wider than the
+    widest gap in the interior."""
+    piv = ex.sparse_pivots(M, m)
+    assert piv[:2] == [M - 1, 0]
+    pts = sorted(piv)
+    gaps = np.diff(pts)
+    if len(gaps) >= 3:
+        assert max(gaps[0], gaps[-1]) <= max(gaps[1:-1])
