@@ -294,6 +294,9 @@ int sg_sqdiff_accum(sg_op_t op, const void* x, const void* xs, double* acc, void
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture on that device.
+ *  - The operator must have been created on the device that is current at
+ *    the call (the array used is the current device's); otherwise the call
+ *    returns SG_ERR_INVALID.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; the call resets what must start at zero itself.  Calls whose
  *    work overlaps on the GPU (other streams, other host threads) race on the
@@ -350,14 +353,18 @@ int sg_guess_update(sg_guess_t g, const void* x, const void* b, void* stream);
  * that restarts needs its history back).  sg_guess_image_bytes: size of the
  * HOST image (a header plus the handle's workspace contents: history columns,
  * projection state and R), 0 for a NULL handle.  sg_guess_export writes the
- * image to ``image`` (HOST, caller-owned); sg_guess_import restores it into a
- * handle created with the same n, s, method, degree and dtype (its own
- * workspace), after which form/update continue exactly as they would have in
- * the exported handle.  Both synchronise with ``stream``.  SG_ERR_INVALID for
- * NULL arguments or an image of another kind of handle. */
+ * image to ``image`` (HOST, caller-owned, sg_guess_image_bytes(g) bytes).
+ * sg_guess_import restores an image of image_bytes bytes into a handle
+ * created with the same n, s, method, degree and dtype -- for projection
+ * handles also the same eps_rel and an operator of the same mesh, degree,
+ * lambda and dtype, under which the stored history is orthonormal -- after
+ * which form/update continue exactly as they would have in the exported
+ * handle.  The header is checked before anything is copied (size, kind,
+ * ring position consistent with an update count); on SG_ERR_INVALID the
+ * handle is unchanged.  Both synchronise with ``stream``. */
 size_t sg_guess_image_bytes(sg_guess_t g);
 int sg_guess_export(sg_guess_t g, void* image, void* stream);
-int sg_guess_import(sg_guess_t g, const void* image, void* stream);
+int sg_guess_import(sg_guess_t g, const void* image, size_t image_bytes, void* stream);
 
 /* Debug/inspection (synchronises ``stream``): current history dimension d
  * (PROJ) or stored-solution count (EXTRAP), and, if R is not NULL, the

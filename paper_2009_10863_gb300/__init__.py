@@ -55,7 +55,7 @@ SIGNATURES = [
     ("sg_guess_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     ("sg_guess_image_bytes", _SZ, [_VP]),
     ("sg_guess_export", _I, [_VP, _VP, _VP]),
-    ("sg_guess_import", _I, [_VP, _VP, _VP]),
+    ("sg_guess_import", _I, [_VP, _VP, _SZ, _VP]),
     ("sg_profile_enable", _I, [_I]),
     ("sg_profile_read", _I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     ("sg_profile_reset", _I, []),
@@ -306,8 +306,8 @@ class Guess:
 
     def restore(self, image):
         """Load a history exported by a handle with the same parameters."""
-        img = np.ascontiguousarray(image, dtype=np.uint8)
-        _check(lib().sg_guess_import(self.h, img.ctypes.data_as(ctypes.c_void_p), _stream()))
+        img = np.ascontiguousarray(image, dtype=np.uint8).reshape(-1)
+        _check(lib().sg_guess_import(self.h, img.ctypes.data_as(ctypes.c_void_p), img.size, _stream()))
 
     def info(self):
         """(d, R or beta as an s x s / s array) -- synchronises."""

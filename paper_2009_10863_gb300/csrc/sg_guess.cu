@@ -917,8 +917,23 @@ struct GuessImageHeader {
   int64_t n;
   int32_t method, s, m, dtype, count, next;
   uint64_t ws_bytes;
+  double eps_rel;                 // projection acceptance threshold
+  int32_t op_ex, op_ey, op_ez, op_p, op_dtype, pad;   // projection: the operator of A X~ = B~
+  double op_lambda;
 };
-constexpr uint64_t kGuessImageMagic = 0x5347475545535331ull;
+constexpr uint64_t kGuessImageMagic = 0x5347475545535332ull;
+
+// The image's operator fields: a projection history is orthonormal only under
+// the operator (mesh, degree, lambda) it was built with; the EXTRAP family has
+// none (zeros).
+void image_op_fields(sg_guess_t g, GuessImageHeader& h) {
+  h.op_ex = h.op_ey = h.op_ez = h.op_p = h.op_dtype = h.pad = 0;
+  h.op_lambda = 0.0;
+  if (is_proj(g->method) && g->op) {
+    h.op_ex = g->op->g.ex; h.op_ey = g->op->g.ey; h.op_ez = g->op->g.ez; h.op_p = g->op->g.p;
+    h.op_dtype = g->op->dtype; h.op_lambda = g->op->lambda;
+  }
+}
 }  // namespace
 
 extern "C" size_t sg_guess_image_bytes(sg_guess_t g) {
@@ -933,6 +948,8 @@ extern "C" int sg_guess_export(sg_guess_t g, void* image, void* stream) {
   h.magic = kGuessImageMagic;
   h.n = g->n; h.method = g->method; h.s = g->s; h.m = g->m; h.dtype = g->dtype;
   h.count = g->count; h.next = g->next; h.ws_bytes = total;
+  h.eps_rel = g->eps_rel;
+  image_op_fields(g, h);
   std::memcpy(image, &h, sizeof(h));
   cudaStream_t s = as_stream(stream);
   if (total > 0)
@@ -942,15 +959,32 @@ extern "C" int sg_guess_export(sg_guess_t g, void* image, void* stream) {
   return SG_OK;
 }
 
-extern "C" int sg_guess_import(sg_guess_t g, const void* image, void* stream) {
+extern "C" int sg_guess_import(sg_guess_t g, const void* image, size_t image_bytes, void* stream) {
   if (!g || !image) return sg_fail(SG_ERR_INVALID, "guess_import: NULL argument");
+  const size_t total = guess_layout(g->n, g->s, g->method, g->dtype).total;
+  if (image_bytes != sizeof(GuessImageHeader) + total)
+    return sg_fail(SG_ERR_INVALID, "guess_import: image of " + std::to_string(image_bytes) + " bytes, this handle's is " +
+                                   std::to_string(sizeof(GuessImageHeader) + total));
   GuessImageHeader h;
   std::memcpy(&h, image, sizeof(h));
-  const size_t total = guess_layout(g->n, g->s, g->method, g->dtype).total;
   if (h.magic != kGuessImageMagic) return sg_fail(SG_ERR_INVALID, "guess_import: not a guess image");
   if (h.n != g->n || h.method != g->method || h.s != g->s || h.m != g->m || h.dtype != g->dtype ||
       h.ws_bytes != total)
     return sg_fail(SG_ERR_INVALID, "guess_import: image of a handle with other n, s, method, degree or dtype");
+  // ring position: update keeps count = min(k, nsl) and next = k mod nsl after
+  // k updates, so next == count until the ring is full; projection handles keep
+  // both at 0 (their state is on the device)
+  const bool ring = is_ring(g->method);
+  const bool pos_ok = ring ? (h.count >= 0 && h.count <= g->nsl && h.next >= 0 && h.next < g->nsl &&
+                              (h.count == g->nsl || h.next == h.count))
+                           : (h.count == 0 && h.next == 0);
+  if (!pos_ok) return sg_fail(SG_ERR_INVALID, "guess_import: ring position out of range (corrupt image)");
+  GuessImageHeader mine{};
+  image_op_fields(g, mine);
+  if (is_proj(g->method) &&
+      (h.eps_rel != g->eps_rel || h.op_ex != mine.op_ex || h.op_ey != mine.op_ey || h.op_ez != mine.op_ez ||
+       h.op_p != mine.op_p || h.op_dtype != mine.op_dtype || h.op_lambda != mine.op_lambda))
+    return sg_fail(SG_ERR_INVALID, "guess_import: projection image built with another operator or eps_rel");
   cudaStream_t s = as_stream(stream);
   if (total > 0)
     SG_CUDA_TRY(cudaMemcpyAsync(g->ws, static_cast<const unsigned char*>(image) + sizeof(h), total,

@@ -645,6 +645,9 @@ extern "C" int sg_pcg_solve_noalloc(sg_op_t op, const void* b, void* x, double t
   int dev = 0;
   SG_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: device index out of range");
+  if (dev != op->device)
+    return sg_fail(SG_ERR_INVALID, "pcg_solve_noalloc: the operator was created on device " +
+                                   std::to_string(op->device) + ", the current device is " + std::to_string(dev));
   void* ptr = nullptr;
   {
     // set-up, once per device with that device current: the host-side name of

@@ -264,35 +264,61 @@ def test_extrap_inplace_guess_into_next_slot(sg):
     assert rel(host(slot), want) <= 1e-12
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("method", ["extrap", "qr", "energy"])
-def test_guess_checkpoint_restore(sg, method):
-    """A history exported after five updates and restored into a fresh handle
-    (its own workspace) forms the same guesses, bit for bit, as the original
-    over three further steps; an image of another kind of handle is refused."""
+def test_guess_checkpoint_restore(sg, method, dtype):
+    """A history exported after six updates of an s = 4 handle (the ring has
+    wrapped) and restored into a fresh handle (its own workspace) forms the same
+    guesses, bit for bit, as the original over three further steps.  Images of
+    another kind of handle, truncated images, forged ring positions and (for
+    projection) images built under another operator are refused before
+    anything is copied: the refusing handle keeps forming its own guesses."""
     E, p, lam = (3, 2, 2), 4, 3.0
-    op = sg.Op(*E, p, lam, "f64")
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    op = sg.Op(*E, p, lam, dtype)
     rng = np.random.default_rng(41)
-    mask = host(op.apply(dev(np.ones(op.n)))) != 0.0
-    xs = [dev(rng.standard_normal(op.n) * mask) for _ in range(8)]
-    bs = [dev(rng.standard_normal(op.n) * mask) for _ in range(3)]
-    kw = dict(m=2) if method == "extrap" else dict(eps_rel=1e-10, op=op)
-    g = sg.Guess(op.n, 4, method, **kw)
-    for x in xs[:5]:
+    mask = host(op.apply(dev(np.ones(op.n), tdt))) != 0.0
+    xs = [dev(rng.standard_normal(op.n) * mask, tdt) for _ in range(9)]
+    bs = [dev(rng.standard_normal(op.n) * mask, tdt) for _ in range(3)]
+    kw = dict(m=2) if method == "extrap" else dict(eps_rel=1e-4 if dtype == "f32" else 1e-10, op=op)
+    g = sg.Guess(op.n, 4, method, dtype=dtype, **kw)
+    for x in xs[:6]:
         g.update(x.clone())
     image = g.export()
-    h = sg.Guess(op.n, 4, method, **kw)
+    h = sg.Guess(op.n, 4, method, dtype=dtype, **kw)
     h.restore(image)
     for k in range(3):
         x0g, x0h = op.zeros(), op.zeros()
         g.form(bs[k], x0g)
         h.form(bs[k], x0h)
         assert torch.equal(x0g, x0h), "guess %d" % k
-        g.update(xs[5 + k].clone())
-        h.update(xs[5 + k].clone())
+        g.update(xs[6 + k].clone())
+        h.update(xs[6 + k].clone())
     assert g.info()[0] == h.info()[0]
-    other = sg.Guess(op.n, 3, method, **kw)
+
+    # refusals leave the target handle as it was
+    other = sg.Guess(op.n, 3, method, dtype=dtype, **kw)
+    for x in xs[:2]:
+        other.update(x.clone())
+    before = op.zeros()
+    other.form(bs[0], before)
+    bad = [image[:-8]]                                   # truncated
+    forged = image.copy()
+    forged[36:40] = np.frombuffer(np.int32(99).tobytes(), np.uint8)   # ring position 'next'
+    bad.append(forged)
+    for img in [image] + bad:
+        with pytest.raises(sg.SGError):
+            other.restore(img)
     with pytest.raises(sg.SGError):
-        other.restore(image)
+        h.restore(forged)
+    after = op.zeros()
+    other.form(bs[0], after)
+    assert torch.equal(before, after)
+    if method != "extrap":                               # another operator (lambda)
+        op2 = sg.Op(*E, p, 2 * lam, dtype)
+        k = sg.Guess(op.n, 4, method, dtype=dtype, eps_rel=kw["eps_rel"], op=op2)
+        with pytest.raises(sg.SGError):
+            k.restore(image)
 
 
 def test_zero_guess(sg):
