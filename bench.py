@@ -10,6 +10,11 @@ one pass of the whole hot path over one right-hand side):
   squares, Sec. 3.2); ZERO, LAST and QR(8) (Algorithm 2) are reported beside.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Profiling drivers (short runs for ncu; they print no bench line):
+  python bench.py --profile-driver ops --elements 16 --dtype f64   each kernel once or a few times
+  python bench.py --profile-driver steps --prof-steps 14          headline steps, launches timed one by one
+  python bench.py --profile-driver batched                        one solve of the four batched systems
 """
 import argparse
 import datetime
@@ -543,6 +548,89 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ profiling drivers
+def profile_ops(sg, torch, args):
+    """Every kernel of the library on one mesh: the operator ``--reps`` times,
+    a few PCG iterations (host-launched, each a separate launch), an
+    EXTRAP(2,s) guess and QR(s) history updates until d = s."""
+    E = args.elements
+    op = sg.Op(E, E, E, args.p, args.lam, args.dtype)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(op.n, dtype=op.dtype, device="cuda", generator=gen)
+    y = op.empty()
+    for _ in range(args.reps):
+        op.apply(x, out=y)
+    b = op.apply(x)
+    xs = op.zeros()
+    sg.profile_reset()
+    sg.profile_enable(True)
+    it, _ = op.pcg(b, xs, 1e-10, maxit=args.pcg_iters)
+    sg.profile_enable(False)
+    t_apply, n_apply = sg.profile_read(sg.PROF_PCG_APPLY)
+    t_upd, n_upd = sg.profile_read(sg.PROF_PCG_UPDATE)
+    g = sg.Guess(op.n, args.s, "extrap", m=2, dtype=args.dtype)
+    q = sg.Guess(op.n, args.s, "qr", eps_rel=1e-6, op=op, dtype=args.dtype)
+    for k in range(args.s + 1):          # independent vectors: the QR history fills to d = s
+        v = x + 0.1 * torch.randn(op.n, dtype=op.dtype, device="cuda", generator=gen)
+        g.update(v)
+        q.update(v)
+    x0 = op.zeros()
+    g.form(None, x0)
+    q.form(b, x0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        op.apply(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    print("nodes %d dtype %s apply %.1f us, pcg iterations %d (step %.1f us, update %.1f us), qr d=%d" %
+          (op.n, args.dtype, 1000 * e0.elapsed_time(e1) / 20, it, 1e3 * t_apply / max(n_apply, 1),
+           1e3 * t_upd / max(n_upd, 1), q.info()[0]))
+
+
+def profile_steps(sg, torch, steps):
+    """Headline time steps with every library launch timed by CUDA events, so
+    the PCG iterations are host launches that a profiler lists one by one."""
+    wl = Workload(sg, torch, steps, torch.device("cuda", 0))
+    op = wl.op
+    g = sg.Guess(op.n, CFG["s"], "extrap", m=2, eps_rel=CFG["tol"], op=op)
+    sg.profile_reset()
+    sg.profile_enable(True)
+    iters = []
+    for k in range(steps):
+        x = g.next_slot()
+        g.form(wl.rhs[k], x)
+        it, _ = op.pcg(wl.rhs[k], x, CFG["tol"], true_residual=False)
+        g.update(x)
+        iters.append(it)
+    torch.cuda.synchronize()
+    sg.profile_enable(False)
+    for name, kid in (("pcg_apply", sg.PROF_PCG_APPLY), ("pcg_update", sg.PROF_PCG_UPDATE),
+                      ("extrap", sg.PROF_EXTRAP)):
+        t, c = sg.profile_read(kid)
+        print("%-10s %5d launches %9.1f us" % (name, c, 1e3 * t))
+    print("iterations per step", iters)
+
+
+def profile_batched(sg, torch):
+    """One solve of the four batched systems from zero (right-hand sides A x for
+    random x), persistent launches replayed as plain graph kernel nodes; no tuning."""
+    meshes = [(c["E"][0], c["E"][1], c["E"][2], c["lam"]) for c in BATCHED]
+    solver = sg.BatchSolver(meshes)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    bs, xs = [], []
+    for c in BATCHED:
+        op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
+        bs.append(op.apply(torch.randn(op.n, dtype=torch.float64, device="cuda", generator=gen)))
+        xs.append(op.zeros())
+    sg.profile_enable(True)
+    outer, inner, rel = solver.solve(bs, xs, 1e-10)
+    torch.cuda.synchronize()
+    sg.profile_enable(False)
+    print("batched: outer", outer, "inner", inner, "relres %.2e" % max(rel))
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -560,7 +648,30 @@ def main():
     ap.add_argument("--batched-warmup", type=int, default=8)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (loss + gradient) timing")
     ap.add_argument("--adjoint-steps", type=int, default=50)
+    ap.add_argument("--profile-driver", choices=["ops", "steps", "batched"], default=None,
+                    help="run a short profiling driver instead of the benchmark")
+    ap.add_argument("--elements", type=int, default=16, help="profile-driver ops: elements per axis")
+    ap.add_argument("--p", type=int, default=7, help="profile-driver ops: degree")
+    ap.add_argument("--lam", type=float, default=1e5, help="profile-driver ops: lambda")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="profile-driver ops: dtype")
+    ap.add_argument("--reps", type=int, default=3, help="profile-driver ops: operator applications")
+    ap.add_argument("--pcg-iters", type=int, default=6, help="profile-driver ops: PCG iterations")
+    ap.add_argument("--s", type=int, default=8, help="profile-driver ops: history size")
+    ap.add_argument("--prof-steps", type=int, default=14, help="profile-driver steps: time steps")
     args = ap.parse_args()
+    if args.profile_driver:
+        import torch
+        import paper_2009_10863_gb300 as sg
+        from paper_2009_10863_gb300 import build as sgbuild
+        sgbuild.build()
+        torch.cuda.set_device(0)
+        if args.profile_driver == "ops":
+            profile_ops(sg, torch, args)
+        elif args.profile_driver == "steps":
+            profile_steps(sg, torch, args.prof_steps)
+        else:
+            profile_batched(sg, torch)
+        return
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
 
