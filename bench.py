@@ -40,6 +40,7 @@ CFG = CONFIGS["c2"]
 HEADLINE = ("extrap", 2)          # EXTRAP(m=2, s=8)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 L2_FLUSH_BYTES = 512 << 20
+CPU_BASELINE_STEPS = 5            # complete oracle steps timed for cpu_baseline (~1.3 s each)
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
 PCG_APPLY_TRAFFIC = 34040320 + 0  # read + write of the not-first MODE 1 launch
@@ -67,6 +68,15 @@ def peaks():
 def workload_name():
     E = CFG["E"]
     return "helmholtz-%dx%dx%d-p%d-fp64-%s" % (E[0], E[1], E[2], CFG["p"], "extrap(2,8)")
+
+
+def sem_flops_per_element(p):
+    """Algorithmic flops of one operator application per element, the affine
+    sum-factorised count: per direction an (p+1)x(p+1) matrix on each of the
+    (p+1)^2 element lines, 2 (p+1)^4 flop, three directions 6 (p+1)^4, plus the
+    O((p+1)^3) pointwise work (mass term, sums, weights) counted as 8 (p+1)^3.
+    p = 7: 28,672 flop per element."""
+    return 6.0 * (p + 1) ** 4 + 8.0 * (p + 1) ** 3
 
 
 def sem_flops_per_node(p):
@@ -482,9 +492,23 @@ def run_method(sg, torch, wl, method, m, s, steps, warmup, flush, prof=False, cl
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(iters_per_step, samples=3, full_iteration_count=False):
-    """Time the FP64 CPU oracle on the same workload: EXTRAP(2,8) guess, PCG
-    start-up and PCG iterations, composed into ms per step."""
+def bench_config(n=None):
+    """The ``config`` object of the JSON line, identical for both arms."""
+    E = CFG["E"]
+    nodes = n if n is not None else (CFG["p"] * E[0] + 1) * (CFG["p"] * E[1] + 1) * (CFG["p"] * E[2] + 1)
+    return {"workload": workload_name(), "elements": list(E), "p": CFG["p"], "nodes": nodes,
+            "lambda": CFG["lam"], "s": CFG["s"], "method": "EXTRAP(2,8)", "tol": CFG["tol"],
+            "criterion": "||r|| <= tol ||b||", "l2": "flushed (512 MiB write) between timed steps",
+            "parallelism": "replicas (one independent sequence per GPU)"}
+
+
+def oracle_steps(steps, warmup):
+    """Complete time steps of the FP64 CPU oracle on the headline workload, each
+    timed with the host clock: the EXTRAP(2,8) guess from the last 8 solutions,
+    the Jacobi-PCG solve from it to ||r|| <= 1e-10 ||b||, and the history update.
+    The history starts from the exact solutions x*(t_1..t_8), so every step has
+    a full ring; right-hand sides (with the bench's noise) are built untimed.
+    Returns per-step milliseconds and CG iterations of the timed steps."""
     from oracle.sem import SemOperator
     from oracle.pcg import pcg
     from oracle import extrap as ex
@@ -496,54 +520,44 @@ def oracle_sample(iters_per_step, samples=3, full_iteration_count=False):
     hist = [modes.field(cx, cy, cz, c["dt"] * k) * op.interior for k in range(1, s + 1)]
     diag = op.diagonal()
     beta = ex.lsq_coeffs(s, m)
-
-    def rhs(k):
+    ms, its = [], []
+    for k in range(s + 1, s + 1 + warmup + steps):
         b = op.apply(modes.field(cx, cy, cz, c["dt"] * k) * op.interior)
-        rms = np.sqrt(np.mean(b * b))
-        return b + c["noise"] * rms * noise(c["seed"], k, op.n) * (b != 0)
-
-    iters_oracle = None
-    if full_iteration_count:
-        b = rhs(s + 1)
-        x0 = ex.extrap_guess(hist, beta)
-        _, iters_oracle, _, _ = pcg(op.apply, diag, b, x0, c["tol"], interior=op.interior)
-        iters_per_step = iters_oracle
-    t_form, t_init, t_it = [], [], []
-    S = 2
-    for k in range(samples):
-        b = rhs(s + 2 + k)
+        b = b + c["noise"] * np.sqrt(np.mean(b * b)) * noise(c["seed"], k, op.n) * (b != 0)
         t0 = time.perf_counter()
         x0 = ex.extrap_guess(hist, beta)
+        x, it, _, _ = pcg(op.apply, diag, b, x0, c["tol"], interior=op.interior)
+        hist.append(x)
+        hist.pop(0)
         t1 = time.perf_counter()
-        pcg(op.apply, diag, b, x0, c["tol"], maxit=0, interior=op.interior)
-        t2 = time.perf_counter()
-        pcg(op.apply, diag, b, x0, c["tol"], maxit=S, interior=op.interior)
-        t3 = time.perf_counter()
-        t_form.append(t1 - t0)
-        t_init.append(t2 - t1)
-        t_it.append(((t3 - t2) - (t2 - t1)) / S)
-    mean = lambda v: sum(v) / len(v)
-    ms = 1e3 * (mean(t_form) + mean(t_init) + iters_per_step * mean(t_it))
-    return ms, iters_per_step, iters_oracle, len(t_form)
+        if k >= s + 1 + warmup:
+            ms.append(1e3 * (t1 - t0))
+            its.append(it)
+    return ms, its
+
+
+def oracle_threads():
+    """Threads the oracle's numpy/BLAS calls may use (the bench pins them to 1)."""
+    return int(os.environ.get("OMP_NUM_THREADS", "1"))
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     t0 = time.perf_counter()
-    ms, its, its_o, ns = oracle_sample(None, samples=max(1, min(args.steps, 5)), full_iteration_count=True)
-    sample = ("FP64 numpy oracle (single thread) on the 16^3 p=7 Helmholtz workload: one full PCG solve "
-              "from the EXTRAP(2,8) guess gives %d iterations; %d sampled steps time the guess, the PCG "
-              "start-up and 2 PCG iterations, composed into ms per step" % (its_o, ns))
-    line = {"metric": METRIC, "value": ms, "unit": "ms/step", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+    ms, its = oracle_steps(args.steps, args.warmup)
+    value = sum(ms) / len(ms)
+    sample = ("FP64 numpy oracle, %d thread(s) of %d host cores: %d untimed + %d timed complete steps of the "
+              "16^3 p=7 Helmholtz sequence (EXTRAP(2,8) guess, Jacobi-PCG to 1e-10, history update), "
+              "host clock per step" % (oracle_threads(), os.cpu_count() or 0, args.warmup, args.steps))
+    line = {"metric": METRIC, "value": value, "unit": "ms/step", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_name(), "elements": list(CFG["E"]), "p": CFG["p"],
-                       "nodes": (7 * 16 + 1) ** 3, "lambda": CFG["lam"], "s": CFG["s"], "tol": CFG["tol"],
-                       "parallelism": "replicas"},
-            "cg_iters_per_step": its,
-            "cpu_baseline": {"value": ms, "unit": "ms/step", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": ms, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "config": bench_config(),
+            "cg_iters_per_step": sum(its) / len(its),
+            "cpu_baseline": {"value": value, "unit": "ms/step", "cores": oracle_threads(),
+                             "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
 
@@ -734,8 +748,11 @@ def main():
     kt_iters = sum(kt["iters"])
     tot_apply, cnt_apply = prof["pcg_apply"]
     avg_apply_ms = tot_apply / max(kt_iters, 1)
-    flop_apply = sem_flops_per_node(p) * n
-    achieved = flop_apply / (avg_apply_ms * 1e-3) / 1e12
+    nel = CFG["E"][0] * CFG["E"][1] * CFG["E"][2]
+    flop_alg = sem_flops_per_element(p) * nel          # the roofline's algorithmic unit
+    flop_apply = sem_flops_per_node(p) * n             # the even-odd kernel's own operator count
+    achieved = flop_alg / (avg_apply_ms * 1e-3) / 1e12
+    achieved_own = flop_apply / (avg_apply_ms * 1e-3) / 1e12
     hbm_gbs, hbm_src = peaks()
     ex_tot, ex_cnt = prof["extrap"]
     ex_bytes = (s + 1) * 8 * n
@@ -746,10 +763,7 @@ def main():
     out = {"metric": METRIC, "value": ms_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(), "elements": list(CFG["E"]), "p": p, "nodes": n,
-                      "lambda": CFG["lam"], "s": s, "method": "EXTRAP(2,8)", "tol": CFG["tol"],
-                      "criterion": "||r|| <= tol ||b||", "l2": "flushed (512 MiB write) between timed steps",
-                      "parallelism": "replicas" if world > 1 else "single"},
+           "config": bench_config(n),
            "cg_iters_per_step": sum(head["iters"]) / len(head["iters"]),
            "max_relres": max(head["rels"]),
            "timed_wall_s": t_wall}
@@ -757,10 +771,18 @@ def main():
     out["roofline"] = {"kernel": "pcg_apply (SEM operator + fused p update, FP64)", "bound": "alu",
                        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PCG_APPLY_TRAFFIC,
+                       "flops_per_launch": flop_alg,
+                       "flop_count": "algorithmic: 6 (p+1)^4 + 8 (p+1)^3 = %d flop per element x %d elements "
+                                     "(dense element-line products)" % (sem_flops_per_element(p), nel),
+                       "achieved_own_count": achieved_own, "frac_own_count": achieved_own / FP64_PEAK_TFLOPS,
+                       "flops_per_launch_own_count": flop_apply,
+                       "own_count": "the even-odd operator's arithmetic: %.1f flop per node x %d nodes "
+                                    "(stricter: the fraction of the FP64 peak the kernel's own operations reach)"
+                                    % (sem_flops_per_node(p), n),
                        "traffic_note": "ncu dram__bytes_read+write per launch (cold reads of z, p, q; "
                                        "p and q writes retire to L2), profiles/kernels_helmholtz16_p7_fp64.md",
                        "algorithmic_bytes_per_launch": 5 * 8 * n,
-                       "flops_per_launch": flop_apply, "avg_launch_ms": avg_apply_ms, "launches": cnt_apply,
+                       "avg_launch_ms": avg_apply_ms, "launches": cnt_apply,
                        "iterations": kt_iters,
                        "timing": "kernel-timing pass: the headline's K steps again, every operator and update "
                                  "launch bracketed by CUDA events on its stream; avg_launch_ms = total launch "
@@ -872,11 +894,14 @@ def main():
                               **run_adjoint(sg, torch, device, args.adjoint_steps))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_cpu, its, _, ns = oracle_sample(out["cg_iters_per_step"], samples=3)
-        out["cpu_baseline"] = {"value": ms_cpu, "unit": "ms/step", "cores": 1, "kind": "oracle",
-                               "sample": "FP64 numpy oracle (single thread), 16^3 p=7 Helmholtz: %d samples "
-                                         "of the EXTRAP(2,8) guess, PCG start-up and 2 PCG iterations, "
-                                         "composed with %.1f iterations per step" % (ns, its)}
+        cms, cits = oracle_steps(CPU_BASELINE_STEPS, 1)
+        out["cpu_baseline"] = {"value": sum(cms) / len(cms), "unit": "ms/step", "cores": oracle_threads(),
+                               "host_cores": os.cpu_count(), "kind": "oracle",
+                               "cg_iters_per_step": sum(cits) / len(cits),
+                               "sample": "FP64 numpy oracle, %d thread(s) of %d host cores: 1 untimed + %d timed "
+                                         "complete steps of the same sequence (EXTRAP(2,8) guess, Jacobi-PCG to "
+                                         "1e-10, history update), host clock per step"
+                                         % (oracle_threads(), os.cpu_count() or 0, CPU_BASELINE_STEPS)}
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -23,6 +23,7 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5
 BATCH_MAX = 4
 MAX_HISTORY, MAX_DEGREE = 16, 8
+NOALLOC_MAX_NODES, NOALLOC_SCRATCH_BYTES = 131072, 6815744
 PROF_SEM, PROF_PCG_APPLY, PROF_PCG_UPDATE, PROF_EXTRAP = 0, 1, 2, 3
 PROF_PROJ_DOTS, PROF_PROJ_LINCOMB, PROF_PROJ_UPDATE = 4, 5, 6
 

@@ -121,3 +121,38 @@ def test_layer_knob_and_deviceless_operator(sg):
         assert L.sg_sem_apply(h, VP(256), VP(512), None) == sg.ERR_STATE
         assert b"without a CUDA device" in L.sg_last_error()
     assert L.sg_op_destroy(h) == 0
+
+
+def test_noalloc_constants_match_header(sg):
+    text = open(HEADER).read()
+    assert int(re.search(r"#define SG_NOALLOC_MAX_NODES (\d+)", text).group(1)) == sg.NOALLOC_MAX_NODES
+    assert int(re.search(r"#define SG_NOALLOC_SCRATCH_BYTES \(?(\d+)", text).group(1)) == sg.NOALLOC_SCRATCH_BYTES
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_noalloc_scratch_holds_every_accepted_operator(sg, p, dtype):
+    """Every operator the allocation-free PCG accepts (at most
+    NOALLOC_MAX_NODES nodes) fits its static scratch array: for degree p and
+    both dtypes, the cubic mesh and the thinnest column mesh (the most reduction
+    partials) just below the node limit.  The workspace query is evaluated on
+    this host (no device: one SM assumed); the bound adds the partials of the
+    largest update grid a GPU with 152 SMs uses (8 CTAs per SM, 4 doubles each)."""
+    L = sg.lib()
+    es = 8 if dtype == 0 else 4
+    meshes = []
+    e = 1
+    while ((p * (e + 1) + 1) ** 3) <= sg.NOALLOC_MAX_NODES:
+        e += 1
+    meshes.append((e, e, e))
+    ez = (sg.NOALLOC_MAX_NODES // (p + 1) ** 2 - 1) // p
+    meshes.append((1, 1, ez))
+    for E in meshes:
+        h = ctypes.c_void_p()
+        assert L.sg_op_create(ctypes.byref(h), *E, p, 1.0, dtype) == sg.OK
+        n = L.sg_op_size(h)
+        assert 0 < n <= sg.NOALLOC_MAX_NODES
+        ws = int(L.sg_pcg_workspace_bytes(h))
+        assert ws >= 5 * es * n
+        assert ws + 8 * 152 * 4 * 8 <= sg.NOALLOC_SCRATCH_BYTES, (E, ws)
+        L.sg_op_destroy(h)

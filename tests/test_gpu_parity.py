@@ -12,7 +12,7 @@ from oracle.pcg import pcg as opcg, REL_B, INITRESID, RHS
 from oracle import extrap as oex
 from oracle.proj import ProjectionQR, ProjectionClassic, ProjectionEnergy
 from oracle.sequence import run_sequence
-from synthetic import Modes, random_vectors, CONFIGS
+from synthetic import Modes, random_vectors, noise, CONFIGS, BATCHED
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -487,10 +487,13 @@ def test_proj_full_size(sg):
 
 def test_headline_sequence_full_size(sg):
     """The 16^3 p = 7 Helmholtz sequence with EXTRAP(2,8) and 1e-10, run as
-    the bench runs it (guess formed in the next ring slot, PCG as one graph
-    launch): every guess equals the oracle's extrapolation of the GPU's earlier
-    solutions, and at two sampled steps the oracle's PCG from the same guess
-    takes the same number of iterations (+-1) to the same solution."""
+    the bench runs it (right-hand sides with the bench's noise, guess formed in
+    the next ring slot, PCG as one graph launch) for 18 steps, so that the
+    steady-state guess from a full ring of 8 solutions is compared 10 times:
+    every guess equals the oracle's extrapolation of the GPU's earlier
+    solutions, and at three sampled steps (one during start-up, two with a full
+    ring) the oracle's PCG from the same guess takes the same number of
+    iterations (+-1) to the same solution."""
     c = CONFIGS["c2"]
     s, m, tol = c["s"], 2, c["tol"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
@@ -500,22 +503,26 @@ def test_headline_sequence_full_size(sg):
     g = sg.Guess(op.n, s, "extrap", m=m)
     diag = ref.diagonal()
     sols = []
-    for k in range(1, 11):
+    full_ring = 0
+    for k in range(1, 19):
         b = ref.apply(modes.field(cx, cy, cz, c["dt"] * k) * ref.interior)
+        b = b + c["noise"] * np.sqrt(np.mean(b * b)) * noise(c["seed"], k, ref.n) * (b != 0)
         x = g.next_slot()
         g.form(dev(b), x)
         x0 = host(x)
         if sols:
             beta = oex.startup_coeffs(len(sols), s, m)
             assert rel(x0, oex.extrap_guess(sols[-s:], beta)) <= 1e-12, "guess at step %d" % k
+            full_ring += len(sols) >= s
         it, _ = op.pcg(dev(b), x, tol)
         xk = host(x)
-        if k in (4, 10):
+        if k in (4, 12, 18):
             xo, ito, _, _ = opcg(ref.apply, diag, b, x0, tol, interior=ref.interior)
             assert abs(it - ito) <= 1, "iterations at step %d" % k
             assert rel(xk, xo) <= (1e-10 if it == ito else 10 * tol)
         g.update(x)
         sols.append(xk)
+    assert full_ring == 10
 
 
 # ---------------------------------------------------------------- whole sequence
@@ -574,6 +581,28 @@ def test_fp32_ir_reaches_fp64_tolerance(sg, E, p, lam, method):
     assert outer >= 2 and inner > 0
     xo, _, _, _ = opcg(ref.apply, ref.diagonal(), b, np.zeros(ref.n), 1e-13, interior=ref.interior)
     assert rel(xg, xo) <= 1e-7
+
+
+@pytest.mark.parametrize("method", ["restart", "replace"])
+def test_fp32_ir_full_size_c3(sg, method):
+    """One mixed-precision solve on the full 32^3 p = 7 Poisson mesh (11.4M
+    nodes, the FP32 operator's multi-layer CTAs and the FP64 residual pass at
+    that size), from the EXTRAP-free zero guess: the FP64 residual measured with
+    the oracle operator meets 1e-10, and the solution agrees with the smooth
+    manufactured one to the accuracy the system's conditioning allows."""
+    c = CONFIGS["c3"]
+    ref = SemOperator(*c["E"], c["p"], c["lam"])
+    cx, cy, cz = ref.coords_1d()
+    xs = Modes(c["seed"], c["modes"], c["kmax"]).field(cx, cy, cz, 0.37) * ref.interior
+    b = ref.apply(xs)
+    ms = sg.MixedSolver(*c["E"], c["p"], c["lam"])
+    x = ms.op64.zeros()
+    outer, inner, relg = ms.solve(dev(b), x, 1e-10, method=method)
+    xg = host(x)
+    rel_oracle = np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b)
+    assert relg <= 1e-10 and rel_oracle <= 1.01e-10
+    assert outer >= 2 and inner > 0
+    assert rel(xg, xs) <= 1e-7
 
 
 def test_residual_replacement_keeps_the_krylov_space(sg):
@@ -651,6 +680,45 @@ def test_batched_ir_solves_every_system(sg):
     # a second solve from the converged solutions: no outer step is needed
     outer2, inner2, relres2 = bs.solve(bvs, xvs, 1e-10)
     assert outer2 == [0, 0, 0, 0] and max(relres2) <= 1e-10
+
+
+def _c4_problems():
+    probs = []
+    for c in BATCHED:
+        ref = SemOperator(*c["E"], c["p"], c["lam"])
+        cx, cy, cz = ref.coords_1d()
+        xs = Modes(c["seed"], 8, 4).field(cx, cy, cz, 0.25) * ref.interior
+        probs.append((c, ref, xs, ref.apply(xs)))
+    return probs
+
+
+def test_batched_full_size_c4_several_items_per_cta(sg):
+    """The four C4 systems (24^3 Poisson, 20^3 / 16^3 / 12^3 Helmholtz, p = 7;
+    19.7M nodes in all) in the persistent kernel, first with the default
+    two-layer work items, then with the autotuner's shape.  Every shape the
+    tuner can pick gives more work items than the grid has CTAs (at least 1728
+    items against at most 4 CTAs x SMs), so CTAs run several items one after
+    another (the shared-memory hand-over between items).  Each system's FP64
+    residual, measured with the oracle operator, meets 1e-10, and its solution
+    agrees with the manufactured one."""
+    probs = _c4_problems()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for zl in (2, 4):
+        items = sum(-(-c["E"][0] // 2) * -(-c["E"][1] // 2) * -(-c["E"][2] // zl) for c, *_ in probs)
+        assert items > 4 * nsm
+    solver = sg.BatchSolver([(c["E"][0], c["E"][1], c["E"][2], c["lam"]) for c, *_ in probs])
+    bvs = [dev(b) for _, _, _, b in probs]
+    for tuned in (False, True):
+        if tuned:
+            zl, bps, ms = solver.tune()
+            assert zl in (1, 2, 3, 4) and 1 <= bps <= 4
+        xvs = [torch.zeros(ref.n, dtype=torch.float64, device="cuda") for _, ref, _, _ in probs]
+        outer, inner, relres = solver.solve(bvs, xvs, 1e-10)
+        for k, (c, ref, xs, b) in enumerate(probs):
+            xg = host(xvs[k])
+            assert relres[k] <= 1e-10 and outer[k] >= 1 and inner[k] > 0
+            assert np.linalg.norm(b - ref.apply(xg)) / np.linalg.norm(b) <= 1.01e-10, "system %d" % k
+            assert rel(xg, xs) <= 1e-7, "system %d" % k
 
 
 def test_batched_tuner_then_mixed_convergence(sg):

@@ -59,6 +59,34 @@ def test_noalloc_matches_workspace_pcg_two_calls(sg):
         assert d <= 1e-10
 
 
+def test_noalloc_largest_accepted_size_against_oracle(sg):
+    """A solve near the array's capacity: 7x7x7 elements of degree 7 (125,000
+    nodes, FP64: five PCG vectors of 1 MB each) against the FP64 oracle's PCG
+    from the same guess -- iterations +-1 and the solution to 1e-10 -- on two
+    calls in a row."""
+    from oracle.sem import SemOperator
+    from oracle.pcg import pcg as opcg
+    E, p, lam = (7, 7, 7), 7, 10.0
+    ref = SemOperator(*E, p, lam)
+    assert ref.n <= sg.NOALLOC_MAX_NODES and ref.n > 0.9 * sg.NOALLOC_MAX_NODES
+    op = sg.Op(*E, p, lam, "f64")
+    rng = np.random.default_rng(5)
+    for call in range(2):
+        xs = rng.standard_normal(ref.n) * ref.interior
+        b = ref.apply(xs)
+        x0 = 0.1 * rng.standard_normal(ref.n) * ref.interior
+        x = torch.tensor(x0, dtype=torch.float64, device="cuda")
+        bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+        rc, it, rr = _noalloc(sg, op, bd, x, 1e-10)
+        torch.cuda.synchronize()
+        assert rc == sg.OK
+        xo, ito, _, _ = opcg(ref.apply, ref.diagonal(), b, x0, 1e-10, interior=ref.interior)
+        assert abs(it - ito) <= 1, "call %d: %d vs %d iterations" % (call, it, ito)
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo) * (1 if it == ito else 10)
+        assert np.linalg.norm(b - ref.apply(xg)) <= 1.0000001e-10 * np.linalg.norm(b)
+
+
 def test_noalloc_fp32_and_size_limit(sg):
     op, b, x0 = _problem(sg, (4, 4, 4), 3, 1.0, 3, "f32")
     x_ref = x0.clone()
