@@ -53,6 +53,7 @@ struct BatchArgs {
   int nblocks;
   cudaGraphConditionalHandle cond;   // WHILE condition of the iteration graph (use_cond)
   int use_cond;
+  int solo_tail;            // use_cond: end the loop when one system is left running
 };
 
 // Grid-wide barrier for a cooperative launch, bounded spin (error flag on expiry).
@@ -239,9 +240,12 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
         }
       }
       if constexpr (COND) {
-        if (A.use_cond) {     // continue while a system runs and no barrier wait expired
-          int more = 0;
-          for (int s = 0; s < A.nseq; ++s) more |= !A.seq[s].st->done;
+        if (A.use_cond) {     // continue while systems run and no barrier wait expired
+          int running = 0;
+          for (int s = 0; s < A.nseq; ++s) running += !A.seq[s].st->done;
+          // with solo_tail the last running system continues in its own
+          // (non-persistent) iteration graph, launched by the host
+          int more = running > (A.solo_tail ? 1 : 0);
           if (*(volatile int*)A.err) more = 0;
           cudaGraphSetConditional(A.cond, more ? 1u : 0u);
         }
@@ -362,6 +366,7 @@ struct sg_batch_s {
   // tuned launch configuration
   int zl, blocks_per_sm, nitems, nblocks, tuned;
   int graph_iters;
+  cudaGraphExec_t solo[SG_BATCH_MAX];   // per-system iteration graphs (single-system tail)
   cudaGraphExec_t graph;
   int graph_ready;
   int graph_while;          // 1: the graph is one WHILE node (one launch per solve)
@@ -376,7 +381,8 @@ int n_tiles(const SemGeom& g, int zl) {
 }
 
 size_t batch_smem() {
-  return sizeof(float) * ((size_t)BTile::NPL * BTile::PY * BTile::PX + 2 * (size_t)BP * BTile::TY * BTile::TX);
+  return sizeof(float) * ((size_t)BTile::NPL * BTile::PY * BTile::template pitch<float>() +
+                          2 * (size_t)BP * BTile::TY * BTile::TX);
 }
 
 struct BLayout {
@@ -462,6 +468,7 @@ int launch_iter(sg_batch_t b, cudaStream_t s, cudaGraphConditionalHandle cond = 
   BatchArgs A = make_args(b);
   A.cond = cond;
   A.use_cond = use_cond;
+  A.solo_tail = use_cond && b->nseq > 1;
   void* params[] = {&A};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->nblocks);
@@ -532,6 +539,7 @@ extern "C" int sg_batch_create(sg_batch_t* out, int nseq, const sg_op_t* ops64, 
   for (int s = 0; s < nseq; ++s) { for (int k = 0; k < 7; ++k) b->off_vec[s][k] = L.vec[s][k]; b->off_r64[s] = L.r64[s]; }
   b->max_items = L.max_items; b->max_blocks = L.max_blocks;
   b->graph_iters = 8;
+  for (int k = 0; k < SG_BATCH_MAX; ++k) b->solo[k] = nullptr;
   b->graph_ready = 0;
   b->graph_while = 0;
   b->graph_prof = 0;
@@ -559,7 +567,31 @@ extern "C" int sg_batch_create(sg_batch_t* out, int nseq, const sg_op_t* ops64, 
 
 extern "C" int sg_batch_destroy(sg_batch_t b) {
   if (b && b->graph_ready) cudaGraphExecDestroy(b->graph);
+  if (b)
+    for (int k = 0; k < SG_BATCH_MAX; ++k)
+      if (b->solo[k]) cudaGraphExecDestroy(b->solo[k]);
   delete b;
+  return SG_OK;
+}
+
+// Remaining iterations of system k alone: its state (iteration count, beta,
+// r.z, direction) continues in a WHILE graph of the FP32 operator step and
+// update on its own vectors (built once per system and workspace).
+int sg_pcg_iteration_graph_f32(sg_op_t op, const PcgIterPtrs<float>& v, cudaGraphExec_t* out);
+
+static int batch_solo(sg_batch_t b, int k, cudaStream_t s) {
+  BatchArgs A = make_args(b);
+  const BatchSeq& S = A.seq[k];
+  if (!b->solo[k]) {
+    PcgIterPtrs<float> v{};
+    v.st = S.st; v.partials = A.partials;
+    v.r = S.r; v.z = S.z; v.p = S.p; v.q = S.q; v.x = S.x; v.invd = S.invd;
+    int rc = sg_pcg_iteration_graph_f32(b->op32[k], v, &b->solo[k]);
+    if (rc) { b->solo[k] = nullptr; return rc; }
+  }
+  k_pcg_state_reset_counters<<<1, 32, 0, s>>>(S.st);
+  SG_LAUNCH_CHECK("k_pcg_state_reset_counters");
+  SG_CUDA_TRY(cudaGraphLaunch(b->solo[k], s));
   return SG_OK;
 }
 
@@ -653,6 +685,22 @@ static int batch_inner(sg_batch_t b, const int* active, const BatchTol& tol, int
       int most = 1;
       for (int k = 0; k < b->nseq; ++k) if (active[k] && poll[k].iter > most) most = poll[k].iter;
       sg_count_launches(most);
+      // the last running system continues alone in its own iteration graph
+      // (operator step + update over that system's grid only), which is cheaper
+      // than persistent launches over the whole batch grid
+      int left = -1, nleft = 0;
+      for (int k = 0; k < b->nseq; ++k)
+        if (active[k] && !poll[k].done) { left = k; ++nleft; }
+      if (nleft == 1) {
+        int rc = batch_solo(b, left, s);
+        if (rc) return rc;
+        const int before = poll[left].iter;
+        SG_CUDA_TRY(cudaMemcpyAsync(&poll[left], &A.seq[left].st->iter, sizeof(PollS), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaStreamSynchronize(s));
+        sg_count_launches(2 * (poll[left].iter - before > 0 ? poll[left].iter - before : 1));
+        done_all = 1;
+        for (int k = 0; k < b->nseq; ++k) done_all &= poll[k].done;
+      }
     }
     if (replays >= max_replays) break;
   }

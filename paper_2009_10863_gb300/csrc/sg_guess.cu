@@ -20,6 +20,7 @@
 // The x~ updates of both CGS passes are merged into one (X~ is not modified
 // in between).  All control (d, R, Givens parameters, the eps test) runs in
 // the last CTA of each sweep, so nothing synchronises with the host.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -111,6 +112,35 @@ struct ExtrapArgs {
   int k;
 };
 
+// FP64 grid-stride sweeps are software pipelined: the loads of the thread's
+// next element are issued before the FP64 work on this one, so memory and the
+// FP64 pipe (2 operations per clock per SM on GB300) overlap instead of
+// alternating.  Such sweeps run 2 CTAs of 256 per SM (PIPE_CTAS_PER_SM), ~9
+// elements per thread at 1.44M nodes, with two register sets of columns.
+constexpr int kPipeMaxCols = 9;   // columns a pipelined sweep holds per register set
+constexpr int PIPE_CTAS_PER_SM = 2;
+
+template <typename T> constexpr bool pipelined(int cols) { return sizeof(T) == 8 && cols <= kPipeMaxCols; }
+
+// The thread's grid-stride elements i < nv: load(i, buf) fills NB vectors,
+// body(i, buf) consumes them; the next element's loads are issued before
+// this element's body runs (its stores come after them in program order).
+template <typename V, int NB, typename LoadF, typename BodyF>
+__device__ __forceinline__ void pipe_loop(int nv, LoadF load, BodyF body) {
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  V cur[NB];
+  if (i < nv) load(i, cur);
+  for (; i < nv; i += stride) {
+    V nxt[NB];
+    const int in = i + stride;
+    if (in < nv) load(in, nxt);
+    body(i, cur);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) cur[k] = nxt[k];
+  }
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_extrap(T* out, const ExtrapArgs<T> a, int n) {
   using V = typename VecT<T>::V;
@@ -120,7 +150,34 @@ __global__ void __launch_bounds__(256) k_extrap(T* out, const ExtrapArgs<T> a, i
   for (int j = 0; j < K; ++j) b[j] = (T)a.beta[j];
   const int nv = n / W;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+  int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (pipelined<T>(K)) {
+    V va[K];
+    if (i0 < nv) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) va[j] = reinterpret_cast<const V*>(a.src[j])[i0];
+    }
+    for (int i = i0; i < nv; i += stride) {
+      const int inext = i + stride;
+      V vb[K];
+      if (inext < nv) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) vb[j] = reinterpret_cast<const V*>(a.src[j])[inext];
+      }
+      V acc;
+#pragma unroll
+      for (int w = 0; w < W; ++w) vel(acc, w) = b[0] * vel(va[0], w);
+#pragma unroll
+      for (int j = 1; j < K; ++j)
+#pragma unroll
+        for (int w = 0; w < W; ++w) vel(acc, w) = fma(b[j], vel(va[j], w), vel(acc, w));
+      reinterpret_cast<V*>(out)[i] = acc;
+#pragma unroll
+      for (int j = 0; j < K; ++j) va[j] = vb[j];
+    }
+    i0 = nv;   // the vector loop is done
+  }
+  for (int i = i0; i < nv; i += stride) {
     V v[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = reinterpret_cast<const V*>(a.src[j])[i];   // all loads in flight
@@ -173,13 +230,28 @@ __device__ __forceinline__ void dots_body(const T* base, size_t stride, const T*
 #pragma unroll
   for (int j = 0; j < D; ++j) acc[j] = 0;
   const int nv = n / W, stride_i = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
-    const V yv = reinterpret_cast<const V*>(y)[i];
+  if constexpr (pipelined<T>(D + 1)) {
+    pipe_loop<V, D + 1>(nv,
+      [&](int i, V (&buf)[D + 1]) {
+        buf[D] = reinterpret_cast<const V*>(y)[i];
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const V cv = colv(base, stride, j)[i];
+        for (int j = 0; j < D; ++j) buf[j] = colv(base, stride, j)[i];
+      },
+      [&](int, V (&buf)[D + 1]) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(yv, w);
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[j] = fma(vel(buf[j], w), vel(buf[D], w), acc[j]);
+      });
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+      const V yv = reinterpret_cast<const V*>(y)[i];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const V cv = colv(base, stride, j)[i];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j] += vel(cv, w) * vel(yv, w);
+      }
     }
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
@@ -216,16 +288,32 @@ __device__ __forceinline__ void lincomb_body(const T* base, size_t stride, const
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
   const int nv = n / W, stride_i = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
-    V xs[SG_NZ(D)];
+  if constexpr (D > 0 && pipelined<T>(D)) {
+    pipe_loop<V, D>(nv,
+      [&](int i, V (&buf)[D]) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) xs[j] = colv(base, stride, j)[i];
-    V acc = vzero<V>();
+        for (int j = 0; j < D; ++j) buf[j] = colv(base, stride, j)[i];
+      },
+      [&](int i, V (&buf)[D]) {
+        V acc = vzero<V>();
 #pragma unroll
-    for (int j = 0; j < D; ++j)
+        for (int j = 0; j < D; ++j)
 #pragma unroll
-      for (int w = 0; w < W; ++w) vel(acc, w) += c[j] * vel(xs[j], w);
-    reinterpret_cast<V*>(out)[i] = acc;
+          for (int w = 0; w < W; ++w) vel(acc, w) = fma(c[j], vel(buf[j], w), vel(acc, w));
+        reinterpret_cast<V*>(out)[i] = acc;
+      });
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+      V xs[SG_NZ(D)];
+#pragma unroll
+      for (int j = 0; j < D; ++j) xs[j] = colv(base, stride, j)[i];
+      V acc = vzero<V>();
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int w = 0; w < W; ++w) vel(acc, w) += c[j] * vel(xs[j], w);
+      reinterpret_cast<V*>(out)[i] = acc;
+    }
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
     T acc = 0;
@@ -275,18 +363,20 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
                                              T (&acc)[SG_NZ(D)]) {
   using V = typename VecT<T>::V;
   constexpr int W = VecT<T>::W;
-    const int nv = n / W, stride_i = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
-    V tv;
-    if (DOTS) tv = reinterpret_cast<const V*>(t)[i];
-    V carry = reinterpret_cast<const V*>(base)[i];
+  const int nv = n / W, stride_i = gridDim.x * blockDim.x;
+  // one element: the D + 1 columns (and t) are loaded before the first new
+  // column is stored -- loads after a store to the same array would wait for
+  // it, a load latency per rotation
+  auto rotate = [&](int i, V (&cols)[D + 2]) {
+    const V tv = cols[D + 1];
+    V carry = cols[0];
     if (!FAST) {
 #pragma unroll
       for (int w = 0; w < W; ++w) vel(carry, w) *= gr.sc0;
     }
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const V nx = colv(base, stride, j + 1)[i];
+      const V nx = cols[j + 1];
       V o;
       if (FAST) {
         // coefficients re-read from shared memory on every element: held in
@@ -316,6 +406,20 @@ __device__ __forceinline__ void givens_sweep(T* base, size_t stride, const T* t,
         for (int w = 0; w < W; ++w) acc[j] += vel(o, w) * vel(tv, w);
       }
       reinterpret_cast<V*>(base + (size_t)j * stride)[i] = o;
+    }
+  };
+  auto load = [&](int i, V (&cols)[D + 2]) {
+    if (DOTS) cols[D + 1] = reinterpret_cast<const V*>(t)[i];
+#pragma unroll
+    for (int j = 0; j <= D; ++j) cols[j] = colv(base, stride, j)[i];
+  };
+  if constexpr (pipelined<T>(D + 2)) {
+    pipe_loop<V, D + 2>(nv, load, rotate);
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+      V cols[D + 2];
+      load(i, cols);
+      rotate(i, cols);
     }
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) {
@@ -366,11 +470,20 @@ __device__ __forceinline__ T vdot(const T* u, const T* t, int n) {
   constexpr int W = VecT<T>::W;
   T nn = 0;
   const int nv = n / W, stride_i = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
-    const V tv = reinterpret_cast<const V*>(t)[i];
-    const V uv = reinterpret_cast<const V*>(u)[i];
+  if constexpr (pipelined<T>(2)) {
+    pipe_loop<V, 2>(nv,
+      [&](int i, V (&buf)[2]) { buf[0] = reinterpret_cast<const V*>(t)[i]; buf[1] = reinterpret_cast<const V*>(u)[i]; },
+      [&](int, V (&buf)[2]) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) nn += vel(uv, w) * vel(tv, w);
+        for (int w = 0; w < W; ++w) nn = fma(vel(buf[1], w), vel(buf[0], w), nn);
+      });
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride_i) {
+      const V tv = reinterpret_cast<const V*>(t)[i];
+      const V uv = reinterpret_cast<const V*>(u)[i];
+#pragma unroll
+      for (int w = 0; w < W; ++w) nn += vel(uv, w) * vel(tv, w);
+    }
   }
   for (int i = nv * W + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride_i) nn += u[i] * t[i];
   return nn;
@@ -380,10 +493,10 @@ __device__ __forceinline__ T vdot(const T* u, const T* t, int n) {
 // restart (Algorithm 1, d = 0 or d >= M), then c1 = B~^T t and ||t||^2
 // (energy: c1 = X~^T t = (X~, x_k)_A and ||x_k||_A^2 = x_k . t).
 template <typename T, bool EN, int DMAX>
-// 3 CTAs per SM (85 registers): the rotation sweep is bound by the loads in
-// flight, and the extra CTA beats the few spills it costs (measured: QR(8)
-// update sweeps 284 -> 267 us at 1.44M nodes)
-__global__ void __launch_bounds__(256, 3) k_proj_upd1(const ProjArgs<T> a) {
+// FP32: 3 CTAs per SM (85 registers): the rotation sweep is bound by the loads
+// in flight, and the extra CTA beats the few spills it costs.  FP64: 2 CTAs
+// per SM with the pipelined sweep's two register sets of columns.
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? PIPE_CTAS_PER_SM : 3) k_proj_upd1(const ProjArgs<T> a) {
   constexpr int RV = DMAX + 1;           // dots, then ||t||^2 at [DMAX]
   __shared__ double sred[32 * RV];
   __shared__ double sR[SG_SMAX * SG_SMAX];
@@ -517,7 +630,29 @@ __device__ __forceinline__ void upd2_body(const ProjArgs<T>& a, const T (&c)[SG_
 #pragma unroll
   for (int j = 0; j < D; ++j) acc[j] = 0;
   const int nv = a.n / W, stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+  int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (!EN && pipelined<T>(D + 1)) {
+    pipe_loop<V, D + 1>(nv,
+      [&](int i, V (&buf)[D + 1]) {
+        buf[D] = reinterpret_cast<const V*>(a.t)[i];
+#pragma unroll
+        for (int j = 0; j < D; ++j) buf[j] = colv(a.B, a.stride, j)[i];
+      },
+      [&](int i, V (&buf)[D + 1]) {
+        V tv = buf[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int w = 0; w < W; ++w) vel(tv, w) = fma(-c[j], vel(buf[j], w), vel(tv, w));
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[j] = fma(vel(buf[j], w), vel(tv, w), acc[j]);
+        reinterpret_cast<V*>(a.t)[i] = tv;
+      });
+    i0 = nv;
+  }
+  for (int i = i0; i < nv; i += stride) {
     V tv = reinterpret_cast<const V*>(a.t)[i];
     V cols[SG_NZ(D)];
 #pragma unroll
@@ -740,7 +875,9 @@ int extrap_form(sg_guess_t g, void* x0, cudaStream_t s) {
   }
   a.k = nt;
   ProfScope ps(PROF_EXTRAP, s);
-  const int nb = reduce_blocks(g->n, VecT<T>::W) * 2;   // up to 8 CTAs of 256 per SM (one wave)
+  // FP32: up to 8 CTAs of 256 per SM (one wave); FP64 (pipelined): 2 per SM
+  int nb = reduce_blocks(g->n, VecT<T>::W) * 2;
+  if (pipelined<T>(nt) && nb > PIPE_CTAS_PER_SM * sg_num_sms()) nb = PIPE_CTAS_PER_SM * sg_num_sms();
   T* out = static_cast<T*>(x0);
   const int n = (int)g->n;
 #define SG_CALL(K) k_extrap<T, K><<<nb, 256, 0, s>>>(out, a, n)
@@ -762,7 +899,9 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
   ProjArgs<T> a = proj_args<T>(g);
   a.v = static_cast<const T*>(b);
   a.out = static_cast<T*>(x0);
-  const int nb = reduce_blocks(g->n, VecT<T>::W);
+  const int nb0 = reduce_blocks(g->n, VecT<T>::W);
+  // FP64 sweeps are pipelined (two register sets): PIPE_CTAS_PER_SM per SM
+  const int nb = sizeof(T) == 8 ? std::min(nb0, PIPE_CTAS_PER_SM * sg_num_sms()) : nb0;
   {
     ProfScope ps(PROF_PROJ_DOTS, s);
     static int w4 = 0, w8 = 0, w16 = 0;
@@ -773,9 +912,10 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
   }
   {
     ProfScope ps(PROF_PROJ_LINCOMB, s);
-    if (g->s <= 4) k_proj_lincomb<T, 4><<<nb * 2, 256, 0, s>>>(a);
-    else if (g->s <= 8) k_proj_lincomb<T, 8><<<nb * 2, 256, 0, s>>>(a);
-    else k_proj_lincomb<T, 16><<<nb * 2, 256, 0, s>>>(a);
+    const int nl = sizeof(T) == 8 ? nb : nb0 * 2;
+    if (g->s <= 4) k_proj_lincomb<T, 4><<<nl, 256, 0, s>>>(a);
+    else if (g->s <= 8) k_proj_lincomb<T, 8><<<nl, 256, 0, s>>>(a);
+    else k_proj_lincomb<T, 16><<<nl, 256, 0, s>>>(a);
     SG_LAUNCH_CHECK("k_proj_lincomb");
   }
   return SG_OK;
@@ -784,9 +924,11 @@ int proj_form(sg_guess_t g, const void* b, void* x0, cudaStream_t s) {
 template <typename T, bool EN, int DMAX>
 int proj_update_sweeps(const ProjArgs<T>& a, int nb, cudaStream_t s) {
   static int w1 = 0, w2 = 0, w3 = 0;
-  k_proj_upd1<T, EN, DMAX><<<one_wave(k_proj_upd1<T, EN, DMAX>, nb, w1), 256, 0, s>>>(a);
+  // FP64 rotation and CGS sweeps are pipelined (two register sets): PIPE_CTAS_PER_SM per SM
+  const int np = sizeof(T) == 8 ? std::min(nb, PIPE_CTAS_PER_SM * sg_num_sms()) : nb;
+  k_proj_upd1<T, EN, DMAX><<<one_wave(k_proj_upd1<T, EN, DMAX>, np, w1), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd1");
-  k_proj_upd2<T, EN, DMAX><<<one_wave(k_proj_upd2<T, EN, DMAX>, nb, w2), 256, 0, s>>>(a);
+  k_proj_upd2<T, EN, DMAX><<<one_wave(k_proj_upd2<T, EN, DMAX>, np, w2), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd2");
   k_proj_upd3<T, EN, DMAX><<<one_wave(k_proj_upd3<T, EN, DMAX>, nb, w3), 256, 0, s>>>(a);
   SG_LAUNCH_CHECK("k_proj_upd3");

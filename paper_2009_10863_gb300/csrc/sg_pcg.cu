@@ -214,27 +214,35 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
     }
   };
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // FP64: two grid-stride elements per pass, so that both elements' ten loads
-  // are in flight together (2 CTAs per SM, see update_blocks); FP32 runs a
-  // full wave and keeps its registers for occupancy
-  for (; W == 2 && i + stride < nv; i += 2 * stride) {
-    const int j = i + stride;
-    V xa = reinterpret_cast<V*>(x)[i], xb = reinterpret_cast<V*>(x)[j];
-    const V pa = reinterpret_cast<const V*>(p)[i], pb = reinterpret_cast<const V*>(p)[j];
-    V ra = reinterpret_cast<V*>(r)[i], rb = reinterpret_cast<V*>(r)[j];
-    const V qa = reinterpret_cast<const V*>(q)[i], qb = reinterpret_cast<const V*>(q)[j];
-    const V da = reinterpret_cast<const V*>(invd)[i], db = reinterpret_cast<const V*>(invd)[j];
-    V za, zb;
-    step(xa, pa, ra, qa, da, za);
-    step(xb, pb, rb, qb, db, zb);
-    reinterpret_cast<V*>(x)[i] = xa;
-    reinterpret_cast<V*>(r)[i] = ra;
-    reinterpret_cast<V*>(z)[i] = za;
-    reinterpret_cast<V*>(x)[j] = xb;
-    reinterpret_cast<V*>(r)[j] = rb;
-    reinterpret_cast<V*>(z)[j] = zb;
+  // FP64 (2 CTAs per SM, each thread ~9 grid-stride elements): software
+  // pipelined -- the five loads of the next element are issued before this
+  // element's FP64 work, so the loads of every warp stay in flight while the
+  // FP64 pipe computes; FP32 runs a full wave and keeps its registers for
+  // occupancy
+  if constexpr (W == 2) {
+    V xa, pa, ra, qa, da;
+    if (i < nv) {
+      xa = reinterpret_cast<V*>(x)[i]; pa = reinterpret_cast<const V*>(p)[i];
+      ra = reinterpret_cast<V*>(r)[i]; qa = reinterpret_cast<const V*>(q)[i];
+      da = reinterpret_cast<const V*>(invd)[i];
+    }
+    for (; i < nv; i += stride) {
+      const int j = i + stride;
+      V xb, pb, rb, qb, db;
+      if (j < nv) {
+        xb = reinterpret_cast<V*>(x)[j]; pb = reinterpret_cast<const V*>(p)[j];
+        rb = reinterpret_cast<V*>(r)[j]; qb = reinterpret_cast<const V*>(q)[j];
+        db = reinterpret_cast<const V*>(invd)[j];
+      }
+      V za;
+      step(xa, pa, ra, qa, da, za);
+      reinterpret_cast<V*>(x)[i] = xa;
+      reinterpret_cast<V*>(r)[i] = ra;
+      reinterpret_cast<V*>(z)[i] = za;
+      xa = xb; pa = pb; ra = rb; qa = qb; da = db;
+    }
   }
-  for (; i < nv; i += stride) {
+  for (; W == 4 && i < nv; i += stride) {
     V xv = reinterpret_cast<V*>(x)[i];
     V rv = reinterpret_cast<V*>(r)[i];
     V zv;
@@ -298,14 +306,7 @@ PcgGraphCache* graph_cache(sg_op_t op) {
 }
 
 template <typename T>
-int build_iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L, cudaGraphExec_t* out) {
-  PcgState* st = reinterpret_cast<PcgState*>(ws + L.state);
-  double* partials = reinterpret_cast<double*>(ws + L.partials);
-  T* r = reinterpret_cast<T*>(ws + L.r);
-  T* z = reinterpret_cast<T*>(ws + L.z);
-  T* p = reinterpret_cast<T*>(ws + L.p);
-  T* q = reinterpret_cast<T*>(ws + L.q);
-  T* invd = reinterpret_cast<T*>(ws + L.invd);
+int build_iteration_graph_ptrs(sg_op_t op, const PcgIterPtrs<T>& v, cudaGraphExec_t* out) {
   const int n = (int)op->n;
   int rc = sg_sem_prepare<T, 1>(op->g);
   if (rc) return rc;
@@ -330,12 +331,12 @@ int build_iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L, cud
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     SemArgs<T> a{};
-    a.x = z; a.out = q; a.out2 = p;
-    a.partials = partials; a.st = st;
+    a.x = v.z; a.out = v.q; a.out2 = v.p;
+    a.partials = v.partials; a.st = v.st;
     rc = sg_sem_launch<T, 1>(op->g, a, cs, 0);
     if (rc == SG_OK) {
-      k_pcg_update<T><<<update_blocks(op->n, Vec<T>::W), 256, 0, cs>>>(nullptr, p, r, q, invd, z, n, st, partials,
-                                                                    cond, 1);
+      k_pcg_update<T><<<update_blocks(op->n, Vec<T>::W), 256, 0, cs>>>(v.x, v.p, v.r, v.q, v.invd, v.z, n, v.st,
+                                                                    v.partials, cond, 1);
       e = cudaGetLastError();
     }
     cudaGraph_t captured = nullptr;
@@ -348,6 +349,20 @@ int build_iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L, cud
   if (rc) return rc;
   if (e != cudaSuccess) return sg_fail(SG_ERR_CUDA, std::string("pcg iteration graph: ") + cudaGetErrorString(e));
   return SG_OK;
+}
+
+template <typename T>
+int build_iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& L, cudaGraphExec_t* out) {
+  PcgIterPtrs<T> v{};
+  v.st = reinterpret_cast<PcgState*>(ws + L.state);
+  v.partials = reinterpret_cast<double*>(ws + L.partials);
+  v.r = reinterpret_cast<T*>(ws + L.r);
+  v.z = reinterpret_cast<T*>(ws + L.z);
+  v.p = reinterpret_cast<T*>(ws + L.p);
+  v.q = reinterpret_cast<T*>(ws + L.q);
+  v.invd = reinterpret_cast<T*>(ws + L.invd);
+  v.x = nullptr;                         // the solution vector recorded in the state
+  return build_iteration_graph_ptrs<T>(op, v, out);
 }
 
 // The cached graph for (op, ws), built on first use; NULL (and the reason in
@@ -379,6 +394,12 @@ cudaGraphExec_t iteration_graph(sg_op_t op, unsigned char* ws, const PcgLayout& 
   return exec;
 }
 }  // namespace
+
+// Iteration graph over explicit vectors (the batched solver's single-system
+// tail, sg_batch.cu): x is updated in place, the loop runs while st->done == 0.
+int sg_pcg_iteration_graph_f32(sg_op_t op, const PcgIterPtrs<float>& v, cudaGraphExec_t* out) {
+  return build_iteration_graph_ptrs<float>(op, v, out);
+}
 
 void sg_pcg_release(sg_op_s* op) {
   if (!op || !op->pcg_graphs) return;

@@ -47,6 +47,13 @@
 #pragma once
 #include "sg_common.cuh"
 
+#ifndef SG_SEM_F32_MINB
+#define SG_SEM_F32_MINB 4   // FP32 operator CTAs per SM the register budget is sized for
+#endif
+#ifndef SG_SEM_F32_PXPAD
+#define SG_SEM_F32_PXPAD 0  // extra words per staged row (FP32 shared-memory pitch)
+#endif
+
 struct PcgState {
   double rz, pq, rr, bb, rr0, thr2;
   double alpha, beta;
@@ -62,6 +69,16 @@ struct PcgState {
 
 enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXIT = 2, PCG_BREAKDOWN = 3 };
 
+// Device vectors of one PCG solve's iterations (x == nullptr: the solution
+// vector recorded in the state by the solve's set-up).
+template <typename T>
+struct PcgIterPtrs {
+  PcgState* st;
+  double* partials;
+  T *r, *z, *p, *q, *x;
+  const T* invd;
+};
+
 template <int P>
 struct SemTile {
   static constexpr int TEX = (P <= 2) ? 8 : (P <= 4 ? 4 : 2);
@@ -69,8 +86,11 @@ struct SemTile {
   static constexpr int TX = TEX * P, TY = TEY * P;
   static constexpr int PX = TX + P + 1, PY = TY + P + 1, NPL = 2 * P + 1;  // ring slots
   static constexpr int NTHREADS = TX * TY;
+  // row pitch of a staged plane in shared memory (>= PX; padding moves the
+  // rows of the y line items onto other banks)
+  template <typename T> static constexpr int pitch() { return sizeof(T) == 4 ? PX + SG_SEM_F32_PXPAD : PX; }
   static constexpr int MINB = (NTHREADS <= 256) ? 3 : 1;   // CTAs per SM to fit registers for
-  template <typename T> static constexpr int minb() { return MINB; }
+  template <typename T> static constexpr int minb() { return sizeof(T) == 4 ? SG_SEM_F32_MINB : MINB; }
   // separate x and y result buffers (2 barriers per layer instead of 4): FP32 only,
   // where shared memory is not the occupancy limit
   template <typename T> static constexpr bool two_w() { return sizeof(T) == 4; }
@@ -88,7 +108,7 @@ struct SemArgs {
   T* out2;        // MODE 1: p (in/out)             MODE 2: z
   double* partials;
   PcgState* st;
-  int zl;         // element layers per CTA
+  int zl;         // element layers per CTA (at most; the grid's z chunks are balanced)
   int final_pass; // MODE 2: 1 = true-residual check (store rr_true only)
 };
 
@@ -249,10 +269,13 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   // it); the item returns at once when it is set.  lead_sync = false: no earlier
   // item used this CTA's shared memory (k_sem), so the leading barrier is omitted.
   using TL = SemTile<P>;
-  constexpr int TX = TL::TX, TY = TL::TY, PX = TL::PX, PY = TL::PY, NPL = TL::NPL;
+  constexpr int TX = TL::TX, TY = TL::TY, PY = TL::PY, NPL = TL::NPL;
+  constexpr int PXW = TL::PX;                    // staged row width
+  constexpr int PX = TL::template pitch<T>();    // its pitch in shared memory
   constexpr int TEX = TL::TEX, TEY = TL::TEY, NT = TL::NTHREADS;
   constexpr int PLANE = PX * PY;
-  constexpr int K = (PLANE + NT - 1) / NT;       // staged elements per thread per plane
+  constexpr int STAGED = PXW * PY;               // staged elements per plane
+  constexpr int K = (STAGED + NT - 1) / NT;      // staged elements per thread per plane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);         // NPL ring slots of PY x PX
   constexpr bool TWO_W = TL::template two_w<T>();
@@ -278,15 +301,16 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   const size_t nxy = (size_t)g.nx * g.ny;
 
   // per-thread staging offsets of the padded plane (same for every plane)
-  int soff[K];
+  int soff[K], sdst[K];
   bool sval[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int i = tid + k * NT;
-    const int py = i / PX, px = i - py * PX;
+    const int py = i / PXW, px = i - py * PXW;
     const int gxk = x0 - P + px, gyk = y0 - P + py;
-    sval[k] = (i < PLANE) && gxk > 0 && gyk > 0 && gxk < g.nx - 1 && gyk < g.ny - 1;
+    sval[k] = (i < STAGED) && gxk > 0 && gyk > 0 && gxk < g.nx - 1 && gyk < g.ny - 1;
     soff[k] = sval[k] ? gxk + g.nx * gyk : 0;
+    sdst[k] = py * PX + px;
   }
   auto stage_plane = [&](int gz) {
     T* plane = S + (size_t)(gz % NPL) * PLANE;
@@ -295,7 +319,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int i = tid + k * NT;
-      if (i < PLANE) cp_async_elem(plane + i, base + soff[k], zok && sval[k]);
+      if (i < STAGED) cp_async_elem(plane + sdst[k], base + soff[k], zok && sval[k]);
     }
   };
 
@@ -512,8 +536,9 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
     s_first = (MODE == 1) ? a.st->first : 1;
   }
   T red[3] = {(T)0, (T)0, (T)0};
-  const int e0 = blockIdx.z * a.zl;
-  const int e1 = min(g.ez, e0 + a.zl);
+  // gridDim.z chunks of element layers, balanced: sizes differ by at most one
+  const int e0 = (int)(((long long)blockIdx.z * g.ez) / gridDim.z);
+  const int e1 = (int)(((long long)(blockIdx.z + 1) * g.ez) / gridDim.z);
   sem_item<T, P, MODE>(g, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red, &s_skip, false);
   if (MODE == 1 && s_skip) return;
 

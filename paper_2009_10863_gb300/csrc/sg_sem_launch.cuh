@@ -9,7 +9,8 @@ int sg_sem_layers(const SemGeom& g, int tex, int tey, int override_zl);
 template <typename T, int P>
 constexpr size_t sem_smem_bytes() {
   using TL = SemTile<P>;
-  return sizeof(T) * ((size_t)TL::NPL * TL::PY * TL::PX + (TL::template two_w<T>() ? 2 : 1) * (size_t)P * TL::TY * TL::TX);
+  return sizeof(T) * ((size_t)TL::NPL * TL::PY * TL::template pitch<T>() +
+                      (TL::template two_w<T>() ? 2 : 1) * (size_t)P * TL::TY * TL::TX);
 }
 
 // Dynamic shared-memory attribute of one instantiation (once per process; it
