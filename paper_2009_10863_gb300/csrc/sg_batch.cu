@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
   __shared__ float s_alpha[NS];
   __shared__ double sred[32 * 2 * NS];
   __shared__ int s_all_done;
+  __shared__ SemTabs<float, BP> s_tabs;
   const int tid = threadIdx.x + BTile::TX * threadIdx.y;
   const int NT = BTile::NTHREADS;
   if (tid == 0) {
@@ -132,7 +133,18 @@ __global__ void __launch_bounds__(BTile::NTHREADS, 3) k_batch_iter(const __grid_
     a.x = S.z; a.out = S.q; a.out2 = S.p;
     float red[3] = {0.f, 0.f, 0.f};
     const int e1 = min(S.g.ez, w.w + S.zl);
-    sem_item<float, BP, 1>(S.g, a, w.y, w.z, w.w, e1, &s_beta[w.x], &s_first[w.x], red);
+    // this system's coefficients into shared memory (after the previous item
+    // is done with the last copy)
+    __syncthreads();
+    {
+      constexpr int NW = (int)(sizeof(SemTabs<float, BP>) / sizeof(float));
+      const float* src = static_cast<const float*>(S.g.tabs);
+      float* dst = reinterpret_cast<float*>(&s_tabs);
+      for (int i = tid; i < NW; i += NT) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    sem_item<float, BP, 1, true>(S.g, s_tabs, a, w.y, w.z, w.w, e1, &s_beta[w.x], &s_first[w.x], red, nullptr,
+                                 false);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
       if (s == w.x) pq[s] += red[0];

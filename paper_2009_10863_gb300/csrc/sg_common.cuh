@@ -84,7 +84,8 @@ struct SemGeom {
   double C[3][SG_PMAX + 1][SG_PMAX + 1];  // per direction x, y, z
   double wl[SG_PMAX + 1];  // assembled 1D mass by local index (wl[0] = w0 + wp)
   double dg[3][SG_PMAX + 1];              // diagonal coefficient by local index
-  const void* tabs;        // device: the operator kernel's weighted even-odd tables (sg_op.cu)
+  const void* tabs;        // device: the operator kernel's coefficients, SemTabs (sg_op.cu)
+  const void* htabs;       // host: the same bytes, passed by value to the operator kernel
   int zl;                  // element layers per operator CTA; 0 = automatic
 };
 
@@ -100,6 +101,7 @@ struct sg_op_s {
   int last_iters;           // iterations of the last PCG solve (sizes the first chunk)
   void* pcg_graphs;         // cached PCG iteration graphs (sg_pcg.cu), released with the operator
   void* d_tabs;             // device copy of the operator kernel's tables (g.tabs)
+  alignas(16) unsigned char htabs[2048];   // host copy (g.htabs), sizeof(SemTabs<T, p>) bytes
 };
 
 // Release the PCG iteration graphs cached on an operator (sg_pcg.cu).

@@ -141,13 +141,14 @@ static void build_geom(sg_op_s* op) {
   g.cm = op->lambda * hx * hy * hz / 8.0;
 }
 
-// The operator kernel's 2p+1 weighted even-odd tables (sem_tables), built in
-// FP64 on the host, rounded to the operator's dtype and copied to the device
-// once; every CTA copies them into shared memory.
+// The operator kernel's coefficients (SemTabs: even-odd tables and weights),
+// built in FP64 on the host and rounded to the operator's dtype.  The host
+// copy is passed by value to every operator launch; the device copy serves
+// the batched kernel's shared-memory tables.
 template <typename T, int P>
 static void fill_tables(const SemGeom& g, std::vector<unsigned char>& buf) {
-  buf.assign(sizeof(EOTab<T, P>) * sem_ntabs<P>(), 0);
-  sem_tables<T, P>(g, reinterpret_cast<EOTab<T, P>*>(buf.data()));
+  buf.assign(sizeof(SemTabs<T, P>), 0);
+  sem_tables<T, P>(g, *reinterpret_cast<SemTabs<T, P>*>(buf.data()));
 }
 
 template <typename T>
@@ -175,6 +176,9 @@ static int upload_tables(sg_op_s* op) {
   std::vector<unsigned char> buf;
   if (op->dtype == SG_F64) fill_tables_p<double>(op->g, buf);
   else fill_tables_p<float>(op->g, buf);
+  if (buf.size() > sizeof(op->htabs)) return sg_fail(SG_ERR_INVALID, "op_create: coefficient tables too large");
+  std::memcpy(op->htabs, buf.data(), buf.size());
+  op->g.htabs = op->htabs;
   cudaError_t e = cudaMalloc(&op->d_tabs, buf.size());
   if (e != cudaSuccess) {
     op->d_tabs = nullptr;

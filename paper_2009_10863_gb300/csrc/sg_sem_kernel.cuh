@@ -142,22 +142,37 @@ __device__ __forceinline__ void load_run(const T* src, T (&dst)[N]) {
   }
 }
 
-// The 2p+1 tables a CTA uses, built once per operator on the host (sg_op.cu)
-// and copied into shared memory by every CTA:
-//   [0]        z: C_z + c_m I, row a multiplied by W_a (W_p = W_0)
-//   [1 + c]    x, for output plane c (local z index c < p): W_c C_x
-//   [1 + p + c] y, for output plane c: W_c C_y
-// so that every line product already carries the z weight W_k of its output
-// nodes and the epilogue multiplies by W_i W_j only.
-template <int P>
-constexpr int sem_ntabs() { return 2 * P + 1; }
+// The operator's coefficients, built once per operator on the host (sg_op.cu):
+//   t[0]  z: C_z + c_m I, row a multiplied by W_a (W_p = W_0) -- the z line
+//         products carry the weight W_k of their output nodes;
+//   t[1]  x: C_x;   t[2]  y: C_y;
+//   w     the assembled 1D mass weights by local index (w[0] = w_0 + w_p).
+// The single-system kernel takes them as a kernel parameter: every CTA and
+// warp reads the same entries at compile-time offsets, so the line products
+// take them as constant-bank operands (no shared-memory table, no loads).  The
+// batched kernel keeps a shared-memory copy (its systems differ per item).
+template <typename T, int P>
+struct __align__(16) SemTabs {
+  EOTab<T, P> t[3];
+  T w[P + 1];
+};
 
 // o[0..P] = C u for one element line (even-odd), coefficients from table t.
 // With ROW, o[0] also receives row p of C applied to the line ul of the
 // element before (the other element of the shared node 0).
 // Per output pair the odd sum starts from the even one, op = E_a + O_a, and
 // o[p-a] = 2 E_a - op: one multiply-add instead of a multiply and two adds.
-template <typename T, int P, bool ROW>
+template <typename T, int N, bool SMEM>
+__device__ __forceinline__ void table_run(const T* src, T (&dst)[N]) {
+  if constexpr (SMEM) {
+    load_run<T, N>(src, dst);     // shared memory: 16-byte loads
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[k] = src[k];   // kernel parameter: constant operands
+  }
+}
+
+template <typename T, int P, bool ROW, bool SMEM>
 __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1], const EOTab<T, P>& t,
                                         T (&o)[P + 1]) {
   using TL = SemTile<P>;
@@ -168,8 +183,8 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1
 #pragma unroll
   for (int a = 0; a < H; ++a) {
     T ce[H], co[H];
-    load_run<T, H>(t.ce[a], ce);
-    load_run<T, H>(t.co[a], co);
+    table_run<T, H, SMEM>(t.ce[a], ce);
+    table_run<T, H, SMEM>(t.co[a], co);
     T e = ce[0] * s[0];
 #pragma unroll
     for (int l = 1; l < H; ++l) e = fma(ce[l], s[l], e);
@@ -180,7 +195,7 @@ __device__ __forceinline__ void line_eo(const T (&u)[P + 1], const T (&ul)[P + 1
     o[P - a] = fma((T)2, e, -op);
     if (ROW && a == 0) {
       T cr[P + 1];
-      load_run<T, P + 1>(t.crow, cr);
+      table_run<T, P + 1, SMEM>(t.crow, cr);
 #pragma unroll
       for (int l = 0; l <= P; ++l) op = fma(cr[l], ul[l], op);
     }
@@ -229,18 +244,17 @@ inline void build_eotab(const SemGeom& g, int d, const double (&rowmul)[P + 1], 
   for (int l = 0; l <= P; ++l) t.crow[l] = (T)Cm[P][l];
 }
 
-// The 2p+1 tables of sem_ntabs (host).
+// The operator's SemTabs (host).
 template <typename T, int P>
-inline void sem_tables(const SemGeom& g, EOTab<T, P>* tabs) {
-  double wz[P + 1], wc[P + 1];
+inline void sem_tables(const SemGeom& g, SemTabs<T, P>& tb) {
+  double wz[P + 1], one[P + 1];
   for (int a = 0; a < P; ++a) wz[a] = g.wl[a];
   wz[P] = g.wl[0];
-  build_eotab<T, P>(g, 2, wz, tabs[0], g.cm);
-  for (int c = 0; c < P; ++c) {
-    for (int a = 0; a <= P; ++a) wc[a] = g.wl[c];
-    build_eotab<T, P>(g, 0, wc, tabs[1 + c]);
-    build_eotab<T, P>(g, 1, wc, tabs[1 + P + c]);
-  }
+  for (int a = 0; a <= P; ++a) one[a] = 1.0;
+  build_eotab<T, P>(g, 2, wz, tb.t[0], g.cm);
+  build_eotab<T, P>(g, 0, one, tb.t[1]);
+  build_eotab<T, P>(g, 1, one, tb.t[2]);
+  for (int a = 0; a <= P; ++a) tb.w[a] = (T)g.wl[a];
 }
 
 // cp.async of one element, zero-filled when !valid (nothing is read then).
@@ -260,10 +274,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // One work item: the CTA's element-aligned xy tile (bxi, byi) over element
 // layers [e0, e1) of one mesh.  Adds this item's reduction terms to red[].
 // Used by k_sem (one item per CTA) and by the persistent batched kernel.
-template <typename T, int P, int MODE>
-__device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, int bxi, int byi, int e0, int e1,
-                                         const T* beta_s, const int* first_s, T (&red)[3],
+template <typename T, int P, int MODE, bool SMEM>
+__device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& tb, const SemArgs<T>& a, int bxi,
+                                         int byi, int e0, int e1, const T* beta_s, const int* first_s, T (&red)[3],
                                          const int* skip_s = nullptr, bool lead_sync = true) {
+  // tb: the operator's coefficients -- a kernel parameter (SMEM = false) or a
+  // shared-memory copy the caller made and published with a barrier (SMEM).
   // beta_s, first_s: shared-memory scalars of the PCG step (MODE 1), read at use.
   // skip_s: shared flag written before the call (the set-up barrier publishes
   // it); the item returns at once when it is set.  lead_sync = false: no earlier
@@ -281,20 +297,10 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   constexpr bool TWO_W = TL::template two_w<T>();
   T* Wb = S + (size_t)NPL * PLANE;               // P planes of TY x TX (x results)
   T* Wy = TWO_W ? Wb + (size_t)P * TY * TX : Wb; // y results (same buffer for FP64)
-  __shared__ EOTab<T, P> sTab[sem_ntabs<P>()];
-  __shared__ T sW[P + 1];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
   if (lead_sync) __syncthreads();                // shared memory of a previous item is free
-  {                                              // the operator's tables (L2-resident), copied
-    constexpr int NW = sem_ntabs<P>() * (int)(sizeof(EOTab<T, P>) / sizeof(T));
-    const T* src = static_cast<const T*>(g.tabs);
-    T* dst = reinterpret_cast<T*>(sTab);
-    for (int i = tid; i < NW; i += NT) dst[i] = __ldg(src + i);
-  }
-  if (tid <= P) sW[tid] = (T)g.wl[tid];
-  __syncthreads();
   if (skip_s && *skip_s) return;
 
   const int x0 = bxi * TX, y0 = byi * TY;
@@ -328,7 +334,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
   const int ia = tx % P, ib = ty % P;
   const bool col_in = (gx < g.nx - 1) && (gy < g.ny - 1);
   const bool col_int = col_in && gx > 0 && gy > 0;
-  const T wxy = sW[ia] * sW[ib];
+  const T wxy = tb.w[ia] * tb.w[ib];
   const size_t colbase = (size_t)gx + (size_t)g.nx * gy;
 
   // prologue: stage the first layer (all p+1 planes)
@@ -369,7 +375,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       const int gz = (e0 - 1) * P + l;
       ub[l] = (gz > 0) ? a.x[(size_t)gx + (size_t)g.nx * gy + nxy * gz] : (T)0;
     }
-    carry = row_dot<T, P>(ub, sTab[0]);
+    carry = row_dot<T, P>(ub, tb.t[0]);
   }
 
   // x / y item coordinates (one item per thread per phase)
@@ -400,7 +406,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       u[l] = S[slot_of(l) * PLANE + (ty + P) * PX + (tx + P)];
     {
       T o[P + 1];
-      line_eo<T, P, false>(u, u, sTab[0], o);
+      line_eo<T, P, false, SMEM>(u, u, tb.t[0], o);
 #pragma unroll
       for (int c = 0; c < P; ++c) acc[c] = o[c];   // includes c_m u (folded into the z tables)
       acc[0] += carry;
@@ -413,7 +419,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = row[l]; ue[l] = row[P + l]; }
-      line_eo<T, P, true>(ue, ul, sTab[1 + xi_c], o);
+      line_eo<T, P, true, SMEM>(ue, ul, tb.t[1], o);
       T* w = Wb + ((size_t)xi_c * TY + xi_r) * TX + xi_e * P;
 #pragma unroll
       for (int c = 0; c < P; ++c) w[c] = o[c];
@@ -440,7 +446,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       T ul[P + 1], ue[P + 1], o[P + 1];
 #pragma unroll
       for (int l = 0; l <= P; ++l) { ul[l] = col[(size_t)l * PX]; ue[l] = col[(size_t)(P + l) * PX]; }
-      line_eo<T, P, true>(ue, ul, sTab[1 + P + yi_c], o);
+      line_eo<T, P, true, SMEM>(ue, ul, tb.t[2], o);
       T* w = Wy + ((size_t)yi_c * TY + yi_e * P) * TX + yi_r;
       if constexpr (TWO_W) {
 #pragma unroll
@@ -451,9 +457,9 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
       }
     }
     __syncthreads();
-    if constexpr (TWO_W) {
+    if constexpr (TWO_W) {   // x results of plane c carry the plane's weight W_c
 #pragma unroll
-      for (int c = 0; c < P; ++c) acc[c] += Wb[((size_t)c * TY + ty) * TX + tx];
+      for (int c = 0; c < P; ++c) acc[c] = fma(tb.w[c], Wb[((size_t)c * TY + ty) * TX + tx], acc[c]);
     }
 
     // ---- combine, weights, epilogue
@@ -461,9 +467,9 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int gz = e * P + c;
-      const T v = acc[c] + Wy[((size_t)c * TY + ty) * TX + tx];
+      const T v = fma(tb.w[c], Wy[((size_t)c * TY + ty) * TX + tx], acc[c]);   // (x +) y results x W_c
       const bool inside = col_int && gz > 0;
-      const T yv = inside ? wxy * v : (T)0;   // W_k is in the tables
+      const T yv = inside ? wxy * v : (T)0;
       if (col_in) {
         const size_t idx = lidx + nxy * (size_t)c;
         if (MODE == 0) {
@@ -524,7 +530,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemArgs<T>& a, 
 
 template <typename T, int P, int MODE>
 __global__ void __launch_bounds__(SemTile<P>::NTHREADS, SemTile<P>::template minb<T>())
-k_sem(const SemGeom g, const SemArgs<T> a) {
+k_sem(const __grid_constant__ SemGeom g, const SemArgs<T> a, const __grid_constant__ SemTabs<T, P> tb) {
   __shared__ double sred[32 * 3];
   __shared__ int s_skip;
   __shared__ T s_beta;
@@ -539,7 +545,21 @@ k_sem(const SemGeom g, const SemArgs<T> a) {
   // gridDim.z chunks of element layers, balanced: sizes differ by at most one
   const int e0 = (int)(((long long)blockIdx.z * g.ez) / gridDim.z);
   const int e1 = (int)(((long long)(blockIdx.z + 1) * g.ez) / gridDim.z);
-  sem_item<T, P, MODE>(g, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red, &s_skip, false);
+  if constexpr (sizeof(T) == 8) {
+    // FP64: the coefficients into shared memory (16-byte loads in the line
+    // products); read from the parameter they would be hoisted into registers
+    // the FP64 kernel does not have
+    __shared__ SemTabs<T, P> s_tb;
+    constexpr int NW = (int)(sizeof(SemTabs<T, P>) / sizeof(T));
+    const T* src = reinterpret_cast<const T*>(&tb);
+    T* dst = reinterpret_cast<T*>(&s_tb);
+    for (int i = tid; i < NW; i += SemTile<P>::NTHREADS) dst[i] = src[i];
+    __syncthreads();          // the tables and the shared scalars above
+    sem_item<T, P, MODE, true>(g, s_tb, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red, &s_skip, false);
+  } else {
+    __syncthreads();          // the shared scalars above
+    sem_item<T, P, MODE, false>(g, tb, a, blockIdx.x, blockIdx.y, e0, e1, &s_beta, &s_first, red, &s_skip, false);
+  }
   if (MODE == 1 && s_skip) return;
 
   if (MODE == 1) {

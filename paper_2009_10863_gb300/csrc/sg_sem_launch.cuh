@@ -1,5 +1,7 @@
 // sg_sem_launch.cuh -- host-side dispatch of k_sem over (dtype, degree, mode).
 #pragma once
+#include <cstring>
+
 #include "sg_sem_kernel.cuh"
 
 // Element layers per CTA: enough CTAs for ~4 per SM, fewer layers means more
@@ -39,7 +41,9 @@ int sg_sem_launch_p(const SemGeom& g, const SemArgs<T>& a0, cudaStream_t s, int 
   const size_t smem = sem_smem_bytes<T, P>();
   int rc = sg_sem_attr_p<T, P, MODE>();
   if (rc) return rc;
-  k_sem<T, P, MODE><<<grid, block, smem, s>>>(g, a);
+  SemTabs<T, P> tb;                              // the coefficients, by value
+  std::memcpy(&tb, g.htabs, sizeof(tb));
+  k_sem<T, P, MODE><<<grid, block, smem, s>>>(g, a, tb);
   SG_LAUNCH_CHECK("k_sem");
   return SG_OK;
 }
