@@ -45,6 +45,8 @@
 // MODE 2: residual: out = r = b - A x, out2 = z = r / diag(A); r.r, r.z, b.b
 //         (final_pass: r, r.r and b.b only -- the true residual).
 #pragma once
+#include <type_traits>
+
 #include "sg_common.cuh"
 
 #ifndef SG_SEM_F32_MINB
@@ -304,7 +306,11 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
   if (skip_s && *skip_s) return;
 
   const int x0 = bxi * TX, y0 = byi * TY;
-  const size_t nxy = (size_t)g.nx * g.ny;
+  // node indices: 32-bit for FP32 (n < 2^31; fewer address instructions,
+  // 62.1 against 66.5 us for y = A x on 32^3), 64-bit for FP64 (whose register
+  // allocation spills with the 32-bit form)
+  using Idx = typename std::conditional<sizeof(T) == 4, int, size_t>::type;
+  const Idx nxy = (Idx)g.nx * g.ny;
 
   // per-thread staging offsets of the padded plane (same for every plane)
   int soff[K], sdst[K];
@@ -321,7 +327,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
   auto stage_plane = [&](int gz) {
     T* plane = S + (size_t)(gz % NPL) * PLANE;
     const bool zok = gz > 0 && gz < g.nz - 1;
-    const T* base = a.x + (zok ? (size_t)gz * nxy : 0);
+    const T* base = a.x + (zok ? (Idx)gz * nxy : 0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int i = tid + k * NT;
@@ -335,7 +341,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
   const bool col_in = (gx < g.nx - 1) && (gy < g.ny - 1);
   const bool col_int = col_in && gx > 0 && gy > 0;
   const T wxy = tb.w[ia] * tb.w[ib];
-  const size_t colbase = (size_t)gx + (size_t)g.nx * gy;
+  const Idx colbase = (Idx)gx + (Idx)g.nx * gy;
 
   // prologue: stage the first layer (all p+1 planes)
   if (e0 < e1) {
@@ -358,7 +364,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
     const bool two = MODE == 1 || !a.final_pass;   // the true-residual pass reads b only
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-      const size_t idx = colbase + nxy * (size_t)(e0 * P + c);
+      const Idx idx = colbase + nxy * (Idx)(e0 * P + c);
       T* sl = S + (size_t)pq_slot(c) * PLANE;
       cp_async_elem(sl + tid, src0 + (col_in ? idx : 0), col_in);
       if (two) cp_async_elem(sl + NT + tid, src1 + (col_in ? idx : 0), col_in);
@@ -373,7 +379,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
 #pragma unroll
     for (int l = 0; l <= P; ++l) {
       const int gz = (e0 - 1) * P + l;
-      ub[l] = (gz > 0) ? a.x[(size_t)gx + (size_t)g.nx * gy + nxy * gz] : (T)0;
+      ub[l] = (gz > 0) ? a.x[colbase + nxy * (Idx)gz] : (T)0;
     }
     carry = row_dot<T, P>(ub, tb.t[0]);
   }
@@ -428,12 +434,12 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
 
     // epilogue operands of this layer's owned nodes, loaded before the y
     // contraction to overlap their latency with it
-    const size_t lidx = colbase + nxy * (size_t)(e * P);
+    const Idx lidx = colbase + nxy * (Idx)(e * P);
     T ea[P], eb[P];
     if (PREF && (MODE == 1 || MODE == 2)) {
 #pragma unroll
       for (int c = 0; c < P; ++c) {
-        const size_t idx = lidx + nxy * (size_t)c;
+        const Idx idx = lidx + nxy * (Idx)c;
         const bool ok = col_in && (MODE == 2 ? (col_int && e * P + c > 0) : !*first_s);
         ea[c] = ok ? (MODE == 1 ? a.out[idx] : a.aux[idx]) : (T)0;
         eb[c] = (ok && (MODE == 1 || !a.final_pass)) ? (MODE == 1 ? a.out2[idx] : a.invd[idx]) : (T)0;
@@ -471,7 +477,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
       const bool inside = col_int && gz > 0;
       const T yv = inside ? wxy * v : (T)0;
       if (col_in) {
-        const size_t idx = lidx + nxy * (size_t)c;
+        const Idx idx = lidx + nxy * (Idx)c;
         if (MODE == 0) {
           a.out[idx] = yv;
         } else if (MODE == 1) {
@@ -513,7 +519,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
       const int z0 = e0 * P, ze = lastz ? g.nz : e1 * P;
       const int wx = xe - x0, wy = ye - y0, wz = ze - z0;
       auto zero_at = [&](int px, int py, int pz) {
-        const size_t idx = (size_t)px + (size_t)g.nx * py + nxy * pz;
+        const Idx idx = (Idx)px + (Idx)g.nx * py + nxy * (Idx)pz;
         a.out[idx] = (T)0;
         if (MODE == 1 || (MODE == 2 && !a.final_pass)) a.out2[idx] = (T)0;
       };
