@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 CPU_BASELINE_STEPS = 5            # complete oracle steps timed for cpu_baseline (~1.3 s each)
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
-PCG_APPLY_TRAFFIC = 34040320 + 0  # read + write of the not-first MODE 1 launch
+PCG_APPLY_TRAFFIC = 33920512 + 512  # read + write of the not-first MODE 1 launch (sem16d capture)
 
 
 def aggregate_max(value, dist, device):
@@ -68,6 +68,14 @@ def peaks():
 def workload_name():
     E = CFG["E"]
     return "helmholtz-%dx%dx%d-p%d-fp64-%s" % (E[0], E[1], E[2], CFG["p"], "extrap(2,8)")
+
+
+def fp64_frac(ops_per_node, n, avg_ms):
+    """Fraction of the FP64 operation rate (2 per clock per SM) a kernel of
+    ops_per_node FP64 operations per node over n nodes reaches in avg_ms."""
+    if not avg_ms:
+        return None
+    return ops_per_node * n / (avg_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
 
 
 def sem_flops_per_element(p):
@@ -790,12 +798,19 @@ def main():
                        "kernel_pass_ms_per_step": sum(kt["ms"]) / len(kt["ms"]),
                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                       "(DFMA measured at 1.256 TFLOP/s, profiles/fp64_pipes_dfma_vs_mma.md)"}
+    ex_avg = ex_tot / max(ex_cnt, 1) if ex_cnt else None
+    up_avg = up_tot / max(kt_iters, 1) if up_cnt else None
     out["guess_kernels"] = {
         "extrap": {"GB_s": ex_gbs, "frac_of_hbm": ex_gbs / hbm_gbs if ex_gbs else None,
-                   "bytes_per_launch": ex_bytes, "launches": ex_cnt},
+                   "bytes_per_launch": ex_bytes, "launches": ex_cnt,
+                   "fp64_ops_per_node": s, "frac_of_fp64_peak": fp64_frac(s, n, ex_avg)},
         "pcg_update": {"GB_s": up_gbs, "frac_of_hbm": up_gbs / hbm_gbs if up_gbs else None,
-                       "bytes_per_launch": 8 * 8 * n, "launches": up_cnt, "iterations": kt_iters},
-        "hbm_peak_GB_s": hbm_gbs, "hbm_peak_source": hbm_src}
+                       "bytes_per_launch": 8 * 8 * n, "launches": up_cnt, "iterations": kt_iters,
+                       "fp64_ops_per_node": 5, "frac_of_fp64_peak": fp64_frac(5, n, up_avg)},
+        "hbm_peak_GB_s": hbm_gbs, "hbm_peak_source": hbm_src,
+        "fp64_peak_Gops": FP64_PEAK_TFLOPS * 1e3 / 2,
+        "fp64_roof": "FP64 operations (DFMA, DMUL, DADD: one each) per node of the kernel's arithmetic at "
+                     "2 per clock per SM (152 SMs, 2.07 GHz)"}
     out["gpu_launches"] = head["launches"]
     if head["clocks"]:
         out["clocks"] = head["clocks"]
@@ -829,13 +844,19 @@ def main():
         # 7M+2 (upd1 with the Givens downdate 4M-1, upd2 M+1, upd3 2M+2)
         rq = run_method(sg, torch, wl, "qr", 0, s, args.steps, args.warmup, flush, prof=True)
         qk = {}
-        for label, kid, words in (("proj_dots", sg.PROF_PROJ_DOTS, s + 1), ("proj_lincomb", sg.PROF_PROJ_LINCOMB, s + 1),
-                                  ("proj_update", sg.PROF_PROJ_UPDATE, 7 * s + 2)):
+        # FP64 operations per node: dots and lincomb one per column; the update
+        # (d = s: downdate of s - 1 rotations on B~ and X~ at 2 each, s - 1 CGS
+        # dots and the norm; then 2 (s - 1) and 2 (s - 1) + 1)
+        upd_ops = 4 * (s - 1) + (s - 1) + 1 + 2 * (s - 1) + 2 * (s - 1) + 1
+        for label, kid, words, ops in (("proj_dots", sg.PROF_PROJ_DOTS, s + 1, s),
+                                       ("proj_lincomb", sg.PROF_PROJ_LINCOMB, s + 1, s),
+                                       ("proj_update", sg.PROF_PROJ_UPDATE, 7 * s + 2, upd_ops)):
             t, c = sg.profile_read(kid)
             avg = t / max(c, 1)
             gbs = words * 8 * n / (avg * 1e-3) / 1e9 if c else None
             qk[label] = {"avg_us": 1e3 * avg, "launch_groups": c, "bytes_per_group": words * 8 * n, "GB_s": gbs,
-                         "frac_of_hbm": gbs / hbm_gbs if gbs else None}
+                         "frac_of_hbm": gbs / hbm_gbs if gbs else None, "fp64_ops_per_node": ops,
+                         "frac_of_fp64_peak": fp64_frac(ops, n, avg if c else None)}
         out["guess_kernels"]["qr(8)"] = qk
         # the paper's two stopping rules (Eqs. StopCritINITRESID, StopCritRHS) against
         # the workload's ||r|| <= tol ||b||, same EXTRAP(2,8) sequence
