@@ -194,7 +194,7 @@ class Workload:
 MIXED_PROF_STEPS = 2
 
 
-def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
+def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode, delta=None):
     """C3-style steps: mode 'ir' = FP32 history + FP32 PCG in restarted FP64
     refinement, 'ru' = the same with FP64 residual replacement instead of
     restarts, 'f64' = FP64 history + FP64 PCG.  Returns per-step ms and iterations.
@@ -226,7 +226,7 @@ def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode):
         g.form(None, slot)
         if mode in ("ir", "ru"):
             sg.convert(slot, x64)
-            o, i, r = ms.solve(b, x64, tol, method="restart" if mode == "ir" else "replace")
+            o, i, r = ms.solve(b, x64, tol, inner_tol=delta, method="restart" if mode == "ir" else "replace")
             sg.convert(x64, slot)
             if timed:
                 outs.append(o)
@@ -873,10 +873,14 @@ def main():
     if not args.no_mixed:
         # the headline workload itself through FP32 PCG with FP64 residual
         # replacement and an FP32 EXTRAP(2,8) history: the same 1e-10 on the
-        # FP64 residual, context beside the FP64 headline
-        r_h = run_mixed(sg, torch, wl, s, 2, args.steps, args.warmup, flush, "ru")
+        # FP64 residual, context beside the FP64 headline.  Replacement
+        # threshold delta = 1e-4: on this mass-dominated Helmholtz system one
+        # FP32 segment reaches 1e-10 (delta 0.1 / 1e-2 / 1e-3 / 1e-4 measured
+        # 1.34 / 1.02 / 1.05 / 0.84 ms/step with 4 / 2 / 2 / 1 FP64 updates)
+        r_h = run_mixed(sg, torch, wl, s, 2, args.steps, args.warmup, flush, "ru", delta=1e-4)
         out["mixed_precision_headline"] = {
-            "workload": workload_name() + " solved by FP32 PCG with FP64 residual replacement, FP32 history",
+            "workload": workload_name() + " solved by FP32 PCG with FP64 residual replacement "
+                        "(delta 1e-4), FP32 history",
             "ms_per_step": r_h["ms"], "inner_fp32_iters_per_step": r_h["iters"],
             "fp64_updates_per_step": r_h["outer"], "max_relres_fp64": r_h["max_relres"],
             "speedup_vs_fp64_headline": ms_step / r_h["ms"], "kernels": r_h["kernels"]}
