@@ -49,7 +49,8 @@ class HeatSequence:
         if x is None:
             x = op.zeros()
         g.form(rhs, x)
-        it, _ = op.pcg(rhs, x, self.tol, maxit=self.maxit)
+        # no true-residual pass: the sequence needs the solution and the count only
+        it, _ = op.pcg(rhs, x, self.tol, maxit=self.maxit, true_residual=False)
         g.update(x)
         iters.append(it)
         return x
@@ -106,7 +107,7 @@ class HeatSequence:
                     gk = gbuf[nstep % 2]
                 nstep += 1
                 g_adj.form(rhs, gk)
-                it, _ = op.pcg(rhs, gk, self.tol, maxit=self.maxit)
+                it, _ = op.pcg(rhs, gk, self.tol, maxit=self.maxit, true_residual=False)
                 g_adj.update(gk)
                 iters_adj.append(it)
                 _check(lib().sg_adjoint_accum(op.h, _ptr(gk), _ptr(x_km1) if k > 0 else None, _ptr(x_k),
