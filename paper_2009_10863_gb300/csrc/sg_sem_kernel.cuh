@@ -283,7 +283,8 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
   // tb: the operator's coefficients -- a kernel parameter (SMEM = false) or a
   // shared-memory copy the caller made and published with a barrier (SMEM).
   // beta_s, first_s: shared-memory scalars of the PCG step (MODE 1), published
-  // by a barrier before the call.
+  // by a barrier before the call and read at each use (held in registers they
+  // cost the kernels more: 1.5 us per FP64 and FP32 step, measured).
   // skip_s: shared flag written before the call (the set-up barrier publishes
   // it); the item returns at once when it is set.  lead_sync = false: no earlier
   // item used this CTA's shared memory (k_sem), so the leading barrier is omitted.
@@ -357,10 +358,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
   // products run (the FP32 kernel prefetches them into registers).
   constexpr bool PREF = sizeof(T) == 4;          // FP64: registers are too tight
   constexpr bool SPF_FITS = 2 * NT <= PLANE;     // a slot holds one plane's two operands
-  // the PCG step's scalars, read once (the shared values do not change during the item)
-  const bool first = (MODE == 1) ? (*first_s != 0) : true;
-  const T beta = (MODE == 1) ? *beta_s : (T)0;
-  const bool spf = SPF_FITS && !PREF && e1 == e0 + 1 && ((MODE == 1 && !first) || MODE == 2);
+  const bool spf = SPF_FITS && !PREF && e1 == e0 + 1 && ((MODE == 1 && !*first_s) || MODE == 2);
   auto pq_slot = [&](int c) { return (e0 * P + P + 1 + c) % NPL; };
   if (spf) {
     const T* src0 = MODE == 1 ? a.out : a.aux;
@@ -444,7 +442,7 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
 #pragma unroll
       for (int c = 0; c < P; ++c) {
         const Idx idx = lidx + nxy * (Idx)c;
-        const bool ok = col_in && (MODE == 2 ? (col_int && e * P + c > 0) : !first);
+        const bool ok = col_in && (MODE == 2 ? (col_int && e * P + c > 0) : !*first_s);
         ea[c] = ok ? (MODE == 1 ? a.out[idx] : a.aux[idx]) : (T)0;
         eb[c] = (ok && (MODE == 1 || !a.final_pass)) ? (MODE == 1 ? a.out2[idx] : a.invd[idx]) : (T)0;
       }
@@ -486,7 +484,8 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
           a.out[idx] = yv;
         } else if (MODE == 1) {
           T qv = yv, pv = u[c];
-          if (!first) {
+          if (!*first_s) {
+            const T beta = *beta_s;
             const T* sl = S + (size_t)pq_slot(c) * PLANE;
             qv += beta * (PREF ? ea[c] : (spf ? sl[tid] : a.out[idx]));
             pv += beta * (PREF ? eb[c] : (spf ? sl[NT + tid] : a.out2[idx]));
