@@ -424,12 +424,12 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
     // epilogue operands of this layer's owned nodes (FP32), loaded before the x
     // and y contractions to overlap their latency with both (issued between x
     // and y instead: PCG step 95.3 -> 97.0 us on 32^3; not at all: 171 us)
-    const Idx lidx = colbase + nxy * (Idx)(e * P);
     T ea[P], eb[P];
     if (PREF && (MODE == 1 || MODE == 2)) {
+      const Idx lidx0 = colbase + nxy * (Idx)(e * P);
 #pragma unroll
       for (int c = 0; c < P; ++c) {
-        const Idx idx = lidx + nxy * (Idx)c;
+        const Idx idx = lidx0 + nxy * (Idx)c;
         const bool ok = col_in && (MODE == 2 ? (col_int && e * P + c > 0) : !*first_s);
         ea[c] = ok ? (MODE == 1 ? a.out[idx] : a.aux[idx]) : (T)0;
         eb[c] = (ok && (MODE == 1 || !a.final_pass)) ? (MODE == 1 ? a.out2[idx] : a.invd[idx]) : (T)0;
@@ -448,6 +448,8 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
       for (int c = 0; c < P; ++c) w[c] = o[c];
     }
     if constexpr (!TWO_W) __syncthreads();      // x results visible to the y items
+
+    const Idx lidx = colbase + nxy * (Idx)(e * P);   // this layer's first owned node
 
     // ---- y: item (plane c, column, element) -> work buffer
     {
