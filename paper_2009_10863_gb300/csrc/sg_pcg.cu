@@ -31,13 +31,17 @@ struct PcgLayout {
 // Grid of the update kernel.  FP64 (vec 2): 2 CTAs of 256 per SM -- its cost
 // is FP64 instructions, and each block's r.r / r.z reduction adds FP64 work in
 // proportion to the block count (8 CTAs per SM: 1.2 additions per node on the
-// 16^3 p = 7 mesh, 2 per SM: 0.3; measured 3.32 -> 3.72 TB/s there).  FP32
-// (vec 4): 8 per SM, a full wave, for memory-level parallelism.  (FP64 with
-// 3, 4, 6 CTAs per SM measured 23.8, 24.4, 27.4 us against 23.6 us.)
+// 16^3 p = 7 mesh, 2 per SM: 0.3; measured 3.32 -> 3.72 TB/s there).  (FP64
+// with 3, 4, 6 CTAs per SM measured 23.8, 24.4, 27.4 us against 23.6 us.)
+// FP32 (vec 4): up to 4 per SM and at least 4 elements per thread: with 8
+// per SM a thread on a small mesh holds one element and spends its time in
+// the launch and the block reduction (measured with compensated sums, same box:
+// 16^3 p = 7 FP32 + replacement step 0.83 -> 0.78 ms, 32^3 122.4 -> 121.4 ms,
+// four batched systems 51.8 -> 49.2 ms against 8 per SM).
 int update_blocks(int64_t n, int vec) {
   int64_t nv = (n + vec - 1) / vec;
-  int64_t b = (nv + 255) / 256;
-  int64_t cap = (vec == 2 ? 2LL : 8LL) * sg_num_sms();
+  int64_t b = vec == 2 ? (nv + 255) / 256 : (nv + 1023) / 1024;
+  int64_t cap = (vec == 2 ? 2LL : 4LL) * sg_num_sms();
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -203,14 +207,26 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   T* __restrict__ x = s_x;
   const T al = (T)s_alpha;
   T rr = 0, rz = 0;
+  // FP32: compensated (Kahan) per-thread sums of r.r and r.z -- their terms are
+  // non-negative, and a plain FP32 running sum over tens of terms per thread
+  // changes CG iteration counts (32^3 p = 7 Poisson, FP32 + replacement: 750
+  // iterations at 37 terms per thread, 777 at 148)
+  T crr = 0, crz = 0;
+  auto kadd = [](T& sum, T& c, T v) { const T y = v - c; const T t = sum + y; c = (t - sum) - y; sum = t; };
   const int nv = n / W;
   const int stride = gridDim.x * blockDim.x;
   auto step = [&](V& xv, const V& pv, V& rv, const V& qv, const V& dv, V& zv) {
-    upd1(xv.x, pv.x, rv.x, qv.x, dv.x, zv.x, al, rr, rz);
-    upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, rr, rz);
     if constexpr (W == 4) {
-      upd1(xv.z, pv.z, rv.z, qv.z, dv.z, zv.z, al, rr, rz);
-      upd1(xv.w, pv.w, rv.w, qv.w, dv.w, zv.w, al, rr, rz);
+      T r4 = 0, z4 = 0;                      // this element's four terms, then one compensated add
+      upd1(xv.x, pv.x, rv.x, qv.x, dv.x, zv.x, al, r4, z4);
+      upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, r4, z4);
+      upd1(xv.z, pv.z, rv.z, qv.z, dv.z, zv.z, al, r4, z4);
+      upd1(xv.w, pv.w, rv.w, qv.w, dv.w, zv.w, al, r4, z4);
+      kadd(rr, crr, r4);
+      kadd(rz, crz, z4);
+    } else {
+      upd1(xv.x, pv.x, rv.x, qv.x, dv.x, zv.x, al, rr, rz);
+      upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, rr, rz);
     }
   };
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,7 +273,7 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
     upd1(xs, p[i], rs, q[i], invd[i], zs, al, rr, rz);
     x[i] = xs; r[i] = rs; z[i] = zs;
   }
-  double v[2] = {(double)rr, (double)rz}, tot[2];
+  double v[2] = {(double)rr - (double)crr, (double)rz - (double)crz}, tot[2];
   if (grid_reduce_last<2>(v, partials, &st->counter[1], sred, tot)) {
     if (threadIdx.x == 0) {
       st->iter += 1;
