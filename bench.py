@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 from synthetic import forcing_basis_indices, adjoint_parameters, BATCHED, BATCHED_COMMON, CONFIGS, Modes, noise  # noqa: E402
 
 METRIC = "ms per time-step solve at 1e-10 rel. residual + CG iters; guess-kernel HBM GB/s"
-CFG = CONFIGS["c2"]
+CFG = CONFIGS["helmholtz_16x16x16_p7"]
 HEADLINE = ("extrap", 2)          # EXTRAP(m=2, s=8)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 L2_FLUSH_BYTES = 512 << 20
@@ -195,7 +195,7 @@ MIXED_PROF_STEPS = 2
 
 
 def run_mixed(sg, torch, wl, s, m, steps, warmup, flush, mode, delta=None):
-    """C3-style steps: mode 'ir' = FP32 history + FP32 PCG in restarted FP64
+    """Mixed-precision steps (32^3 Poisson shape): mode 'ir' = FP32 history + FP32 PCG in restarted FP64
     refinement, 'ru' = the same with FP64 residual replacement instead of
     restarts, 'f64' = FP64 history + FP64 PCG.  Returns per-step ms and iterations.
     The timed steps run the solves as in production (iterations in graph
@@ -260,7 +260,7 @@ def run_adjoint(sg, torch, device, steps):
     Targets come from a forward run with theta*; the gradient is taken at
     theta = theta*/2.  Timed with CUDA events after one untimed evaluation."""
     from paper_2009_10863_gb300.adjoint import HeatSequence, SequenceLoss
-    c = CONFIGS["c5"]
+    c = CONFIGS["heat_16x16x16_p7"]
     E, p, lam, dt, nparam = c["E"], c["p"], c["lam"], c["dt"], c["modes"]
     seq = HeatSequence(*E, p, tol=c["tol"], s=c["s"], m=2, checkpoint=10)
     op = seq.op(lam)
@@ -895,7 +895,7 @@ def main():
             "ms_per_step": r_h["ms"], "inner_fp32_iters_per_step": r_h["iters"],
             "fp64_updates_per_step": r_h["outer"], "max_relres_fp64": r_h["max_relres"],
             "speedup_vs_fp64_headline": ms_step / r_h["ms"], "kernels": r_h["kernels"]}
-        c3 = CONFIGS["c3"]
+        c3 = CONFIGS["poisson_32x32x32_p7"]
         del wl
         torch.cuda.empty_cache()
         w3 = Workload(sg, torch, args.mixed_warmup + args.mixed_steps + MIXED_PROF_STEPS, device, cfg=c3)

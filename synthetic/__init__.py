@@ -18,13 +18,13 @@ import numpy as np
 
 # name: (elements per direction, degree p, lambda, steps, dt, modes, kmax, s, tol)
 CONFIGS = {
-    "c1": dict(E=(4, 4, 4), p=3, lam=0.0, steps=20, dt=0.01, modes=8, kmax=4, s=4,
+    "poisson_4x4x4_p3": dict(E=(4, 4, 4), p=3, lam=0.0, steps=20, dt=0.01, modes=8, kmax=4, s=4,
                tol=1e-8, noise=0.0, seed=1),
-    "c2": dict(E=(16, 16, 16), p=7, lam=1.0 / (1e-2 * 1e-3), steps=200, dt=1e-3,
+    "helmholtz_16x16x16_p7": dict(E=(16, 16, 16), p=7, lam=1.0 / (1e-2 * 1e-3), steps=200, dt=1e-3,
                modes=32, kmax=6, s=8, tol=1e-10, noise=1e-6, seed=2),
-    "c3": dict(E=(32, 32, 32), p=7, lam=0.0, steps=100, dt=0.01, modes=8, kmax=4, s=8,
+    "poisson_32x32x32_p7": dict(E=(32, 32, 32), p=7, lam=0.0, steps=100, dt=0.01, modes=8, kmax=4, s=8,
                tol=1e-10, noise=0.0, seed=3),
-    "c5": dict(E=(16, 16, 16), p=7, lam=1.0 / (1e-2 * 1e-3), steps=50, dt=1e-3,
+    "heat_16x16x16_p7": dict(E=(16, 16, 16), p=7, lam=1.0 / (1e-2 * 1e-3), steps=50, dt=1e-3,
                modes=64, kmax=8, s=6, tol=1e-10, noise=0.0, seed=5),
 }
 

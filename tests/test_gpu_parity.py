@@ -116,7 +116,7 @@ def test_diagonal(sg, E, p, lam):
 
 def test_sem_apply_full_size_fp64_helmholtz(sg):
     """16^3 elements, p = 7, lambda = 1e5: the FP64 Helmholtz operator at full size."""
-    c = CONFIGS["c2"]
+    c = CONFIGS["helmholtz_16x16x16_p7"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
     cx, cy, cz = ref.coords_1d()
@@ -129,7 +129,7 @@ def test_sem_apply_full_size_fp64_helmholtz(sg):
 
 def test_sem_apply_full_size_fp32_poisson(sg):
     """32^3 elements, p = 7 Poisson in FP32 (the mixed-precision operator)."""
-    c = CONFIGS["c3"]
+    c = CONFIGS["poisson_32x32x32_p7"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     op = sg.Op(*c["E"], c["p"], c["lam"], "f32")
     # a random field: a smooth one cancels strongly in A x (||A x|| << sum |terms|),
@@ -466,7 +466,7 @@ def test_proj_rejects_dependent_vector(sg):
 
 def test_proj_full_size(sg):
     """QR(8) at 16^3 elements, p = 7 (1.44M nodes): ten updates, guesses vs the oracle."""
-    c = CONFIGS["c2"]
+    c = CONFIGS["helmholtz_16x16x16_p7"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
     cx, cy, cz = ref.coords_1d()
@@ -494,7 +494,7 @@ def test_headline_sequence_full_size(sg):
     solutions, and at three sampled steps (one during start-up, two with a full
     ring) the oracle's PCG from the same guess takes the same number of
     iterations (+-1) to the same solution."""
-    c = CONFIGS["c2"]
+    c = CONFIGS["helmholtz_16x16x16_p7"]
     s, m, tol = c["s"], 2, c["tol"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     op = sg.Op(*c["E"], c["p"], c["lam"], "f64")
@@ -547,7 +547,7 @@ def _gpu_sequence(sg, c, method, s, m, rhs, dtype="f64"):
 @pytest.mark.parametrize("method,mcode", [("zero", 0), ("last", 1), ("extrap", 2), ("qr", 3)])
 def test_c1_sequence_end_to_end(sg, method, mcode):
     """The 4^3-element, p = 3 Poisson sequence (20 steps, s = 4, tol 1e-8)."""
-    c = CONFIGS["c1"]
+    c = CONFIGS["poisson_4x4x4_p3"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     cx, cy, cz = ref.coords_1d()
     modes = Modes(c["seed"], c["modes"], c["kmax"])
@@ -590,7 +590,7 @@ def test_fp32_ir_full_size_c3(sg, method):
     that size), from the EXTRAP-free zero guess: the FP64 residual measured with
     the oracle operator meets 1e-10, and the solution agrees with the smooth
     manufactured one to the accuracy the system's conditioning allows."""
-    c = CONFIGS["c3"]
+    c = CONFIGS["poisson_32x32x32_p7"]
     ref = SemOperator(*c["E"], c["p"], c["lam"])
     cx, cy, cz = ref.coords_1d()
     xs = Modes(c["seed"], c["modes"], c["kmax"]).field(cx, cy, cz, 0.37) * ref.interior
@@ -693,7 +693,7 @@ def _c4_problems():
 
 
 def test_batched_full_size_c4_several_items_per_cta(sg):
-    """The four C4 systems (24^3 Poisson, 20^3 / 16^3 / 12^3 Helmholtz, p = 7;
+    """The four batched systems (24^3 Poisson, 20^3 / 16^3 / 12^3 Helmholtz, p = 7;
     19.7M nodes in all) in the persistent kernel, first with the default
     two-layer work items, then with the autotuner's shape.  Every shape the
     tuner can pick gives more work items than the grid has CTAs (at least 1728
