@@ -205,7 +205,9 @@ int sg_ir_solve(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, 
  * Same operators, vectors, workspace (sg_ir_workspace_bytes) and errors as
  * sg_ir_solve.  max_updates bounds the FP64 updates, maxit_inner the FP32
  * iterations in total.  updates, inner_iters, relres: HOST outputs, may be
- * NULL.  Synchronises with ``stream`` once per update. */
+ * NULL.  Synchronises with ``stream`` once per update (once in all when the
+ * guess already meets tol: the first inner solve is enqueued before the host
+ * sees the initial residual and does no work then). */
 int sg_ir_solve_ru(sg_op_t op64, sg_op_t op32, const void* b, void* x, double tol, double delta,
                    int max_updates, int maxit_inner, void* workspace, int* updates, int* inner_iters,
                    double* relres, void* stream);
