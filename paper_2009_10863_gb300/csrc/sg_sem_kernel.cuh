@@ -422,8 +422,8 @@ __device__ __forceinline__ void sem_item(const SemGeom& g, const SemTabs<T, P>& 
     }
 
     // epilogue operands of this layer's owned nodes (FP32), loaded before the x
-    // and y contractions to overlap their latency with both (issued between x
-    // and y instead: PCG step 95.3 -> 97.0 us on 32^3; not at all: 171 us)
+    // and y contractions to overlap their latency with both (PCG step on 32^3:
+    // 95.3 us; issued between x and y, 97.0 us; without the prefetch, 171 us)
     T ea[P], eb[P];
     if (PREF && (MODE == 1 || MODE == 2)) {
       const Idx lidx0 = colbase + nxy * (Idx)(e * P);
