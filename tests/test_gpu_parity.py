@@ -641,6 +641,10 @@ def test_residual_replacement_edge_cases(sg):
     x = ms.op64.zeros()                           # update limit -> NOT_CONVERGED, best iterate kept
     o, inner, relg = ms.solve(b, x, 1e-10, inner_tol=0.5, max_outer=1, method="replace")
     assert o == 1 and relg > 1e-10
+    bn = b.clone()                                # non-finite residual: breakdown, reported, no hang
+    bn[bn.numel() // 2] = float("nan")            # the centre node (interior)
+    with pytest.raises(sg.SGError):
+        ms.solve(bn, ms.op64.zeros(), 1e-10, method="replace")
     with pytest.raises(ValueError):
         ms.solve(b, x, 1e-10, method="nope")
 
