@@ -198,7 +198,15 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   __shared__ double s_alpha;
   __shared__ T* s_x;
   __shared__ double sred[64];
-  if (threadIdx.x == 0) { s_skip = st->done; s_alpha = st->alpha; s_x = x_arg ? x_arg : static_cast<T*>(st->xvec); }
+  // the state the reduction's tail needs, read at the start (no block of this
+  // kernel changes it before the tail): no dependent loads in the serial tail
+  __shared__ double s_rz, s_thr2;
+  __shared__ int s_iter, s_maxit, s_strict;
+  if (threadIdx.x == 0) {
+    s_skip = st->done; s_alpha = st->alpha; s_x = x_arg ? x_arg : static_cast<T*>(st->xvec);
+    s_rz = st->rz; s_thr2 = st->thr2; s_iter = st->iter; s_maxit = st->maxit;
+    s_strict = st->criterion != SG_STOP_REL_B;
+  }
   __syncthreads();
   if (s_skip) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -276,18 +284,20 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   double v[2] = {(double)rr - (double)crr, (double)rz - (double)crz}, tot[2];
   if (grid_reduce_last<2>(v, partials, &st->counter[1], sred, tot)) {
     if (threadIdx.x == 0) {
-      st->iter += 1;
+      const int it = s_iter + 1;
+      st->iter = it;
       st->rr = tot[0];
-      const bool strict = st->criterion != SG_STOP_REL_B;
-      const bool conv = strict ? (tot[0] < st->thr2) : (tot[0] <= st->thr2);
-      if (!isfinite(tot[0]) || !isfinite(tot[1])) { st->status = PCG_BREAKDOWN; st->done = 1; }
-      else if (conv) { st->status = PCG_CONVERGED; st->done = 1; }
+      const bool conv = s_strict ? (tot[0] < s_thr2) : (tot[0] <= s_thr2);
+      int done = 0;
+      if (!isfinite(tot[0]) || !isfinite(tot[1])) { st->status = PCG_BREAKDOWN; done = 1; }
+      else if (conv) { st->status = PCG_CONVERGED; done = 1; }
       else {
-        st->beta = tot[1] / st->rz;
+        st->beta = tot[1] / s_rz;
         st->rz = tot[1];
-        if (st->iter >= st->maxit) { st->status = PCG_MAXIT; st->done = 1; }
+        if (it >= s_maxit) { st->status = PCG_MAXIT; done = 1; }
       }
-      if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+      if (done) st->done = 1;
+      if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
     }
   }
 }

@@ -546,11 +546,13 @@ k_sem(const __grid_constant__ SemGeom g, const SemArgs<T> a, const __grid_consta
   __shared__ int s_skip;
   __shared__ T s_beta;
   __shared__ int s_first;
+  __shared__ double s_rz;     // MODE 1: r.z for alpha in the reduction's tail, read at the start
   const int tid = threadIdx.x + SemTile<P>::TX * threadIdx.y;
   if (tid == 0) {             // published by the table set-up barrier inside sem_item
     s_skip = (MODE == 1) ? a.st->done : 0;
     s_beta = (MODE == 1) ? (T)a.st->beta : (T)0;
     s_first = (MODE == 1) ? a.st->first : 1;
+    if (MODE == 1) s_rz = a.st->rz;
   }
   T red[3] = {(T)0, (T)0, (T)0};
   // gridDim.z chunks of element layers, balanced: sizes differ by at most one
@@ -585,7 +587,7 @@ k_sem(const __grid_constant__ SemGeom g, const SemArgs<T> a, const __grid_consta
           st->status = PCG_BREAKDOWN;
           st->done = 1;
         } else {
-          st->alpha = st->rz / pq;
+          st->alpha = s_rz / pq;
         }
       }
     }
