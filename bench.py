@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 CPU_BASELINE_STEPS = 5            # complete oracle steps timed for cpu_baseline (~1.3 s each)
 # DRAM bytes per launch of the dominant kernel (k_sem<double,7,1>, not the first
 # PCG iteration) from one ncu capture of the current kernel; None once it changes
-PCG_APPLY_TRAFFIC = 33920512 + 512  # read + write of the not-first MODE 1 launch (sem16d capture)
+PCG_APPLY_TRAFFIC = 33921792 + 256  # read + write of the not-first MODE 1 launch (sem16d capture)
 
 
 def aggregate_max(value, dist, device):
