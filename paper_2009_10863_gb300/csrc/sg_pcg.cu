@@ -202,6 +202,19 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   // kernel changes it before the tail): no dependent loads in the serial tail
   __shared__ double s_rz, s_thr2;
   __shared__ int s_iter, s_maxit, s_strict;
+  const int nv = n / W;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // FP64: the first element's p, r, q and 1/diag loads go out before the state
+  // is read and published (x's address comes from the state), so their latency
+  // overlaps the state read at the start of this one-wave launch
+  using VA = typename std::conditional<W == 2, V, char>::type;
+  VA xa, pa, ra, qa, da;
+  if constexpr (W == 2) {
+    if (i < nv) {
+      pa = reinterpret_cast<const V*>(p)[i]; ra = reinterpret_cast<V*>(r)[i];
+      qa = reinterpret_cast<const V*>(q)[i]; da = reinterpret_cast<const V*>(invd)[i];
+    }
+  }
   if (threadIdx.x == 0) {
     s_skip = st->done; s_alpha = st->alpha; s_x = x_arg ? x_arg : static_cast<T*>(st->xvec);
     s_rz = st->rz; s_thr2 = st->thr2; s_iter = st->iter; s_maxit = st->maxit;
@@ -221,7 +234,6 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
   // iterations at 37 terms per thread, 777 at 148)
   T crr = 0, crz = 0;
   auto kadd = [](T& sum, T& c, T v) { const T y = v - c; const T t = sum + y; c = (t - sum) - y; sum = t; };
-  const int nv = n / W;
   const int stride = gridDim.x * blockDim.x;
   auto step = [&](V& xv, const V& pv, V& rv, const V& qv, const V& dv, V& zv) {
     if constexpr (W == 4) {
@@ -237,19 +249,13 @@ k_pcg_update(T* __restrict__ x_arg, const T* __restrict__ p, T* __restrict__ r, 
       upd1(xv.y, pv.y, rv.y, qv.y, dv.y, zv.y, al, rr, rz);
     }
   };
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
   // FP64 (2 CTAs per SM, each thread ~9 grid-stride elements): software
   // pipelined -- the five loads of the next element are issued before this
   // element's FP64 work, so the loads of every warp stay in flight while the
   // FP64 pipe computes; FP32 runs a full wave and keeps its registers for
   // occupancy
   if constexpr (W == 2) {
-    V xa, pa, ra, qa, da;
-    if (i < nv) {
-      xa = reinterpret_cast<V*>(x)[i]; pa = reinterpret_cast<const V*>(p)[i];
-      ra = reinterpret_cast<V*>(r)[i]; qa = reinterpret_cast<const V*>(q)[i];
-      da = reinterpret_cast<const V*>(invd)[i];
-    }
+    if (i < nv) xa = reinterpret_cast<V*>(x)[i];
     for (; i < nv; i += stride) {
       const int j = i + stride;
       V xb, pb, rb, qb, db;
